@@ -1,0 +1,168 @@
+/*
+ * nrpf.h - batched Newton-Raphson AC power flow on one GPU (C ABI).
+ *
+ * Many power flows whose admittance matrices share one sparsity pattern are
+ * solved at once (Wang, Wende-von Berg & Braun, "Fast Parallel Newton-Raphson
+ * Power Flow Solver for Large Number of System Calculations with CPU and GPU",
+ * Sec. 3).  A plan does the symbolic work once per pattern (Sec. 4.1: ordering,
+ * fill-in pattern, static lookup, level schedules); each solve then runs, per
+ * Newton iteration and for the whole batch, the nodal power mismatch (Alg. 1),
+ * the Jacobian refill straight into the permuted LU workspace (Sec. 3.1.2),
+ * the LU refactorisation without pivoting (Sec. 4.3, Eq. 3), forward/backward
+ * substitution (Sec. 4.3.3, Eq. 2) and the voltage update (Sec. 3, step 4).
+ *
+ * Conventions shared by every entry point:
+ *  - All functions return an int status: NRPF_OK (0) or a negative NRPF_ERR_*
+ *    code; pf_status_str() names it.  No function throws or aborts.
+ *  - "host" pointers are ordinary CPU memory read during the call; "device"
+ *    pointers are CUDA global memory of the current device, owned by the
+ *    caller, and are accessed asynchronously on the caller's stream.
+ *  - Complex arrays are interleaved (re, im) float64 pairs, row-major [B, n]:
+ *    element (b, i) is at offset 2*(b*n + i).
+ *  - Bus-type codes follow MATPOWER: 3 = slack, 2 = PV, 1 = PQ.
+ *  - Per-instance status codes: 0 converged, 1 reached maxit, 2 numerical
+ *    failure (zero or non-finite pivot, non-finite mismatch or step).
+ */
+#ifndef NRPF_H
+#define NRPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define NRPF_OK 0
+#define NRPF_ERR_ARG (-1)        /* null pointer, bad size, bad option       */
+#define NRPF_ERR_PATTERN (-2)    /* invalid Ybus pattern or bus types        */
+#define NRPF_ERR_NOMEM (-3)      /* host or device allocation failed         */
+#define NRPF_ERR_CUDA (-4)       /* a CUDA runtime call failed               */
+#define NRPF_ERR_CAPACITY (-5)   /* batch larger than the plan's capacity    */
+
+/* ---- per-instance outcomes ---- */
+#define NRPF_CONVERGED 0
+#define NRPF_MAXIT 1
+#define NRPF_FAILED 2
+
+/* ---- options ---- */
+#define NRPF_LU_FP64 0           /* LU refactor and FS/BS in float64           */
+#define NRPF_LU_FP32 1           /* LU refactor and FS/BS in float32 (inexact
+                                    Newton step; mismatch/update stay float64) */
+#define NRPF_ORDER_AMD 0         /* approximate minimum degree on the bus graph */
+#define NRPF_ORDER_NATURAL 1     /* bus order as given (tests)                  */
+
+typedef struct pf_options {
+  int lu_precision;    /* NRPF_LU_FP64 | NRPF_LU_FP32                              */
+  int ordering;        /* NRPF_ORDER_AMD | NRPF_ORDER_NATURAL                      */
+  double dense_frac;   /* AMD stops once the cheapest vertex touches this share of
+                          the remaining unknowns; the rest is one dense block.
+                          0 selects the default (0.7); >= 1 disables the block. */
+  int panel;           /* dense-block panel width (4, 8 or 16); 0 = default 8      */
+  int max_batch;       /* batch capacity to allocate at plan creation; 0 = grow on
+                          first solve (that call then allocates device memory)    */
+} pf_options;
+
+typedef struct pf_plan pf_plan;   /* opaque; owns its device arrays and workspace */
+
+typedef struct pf_plan_info {
+  int n;               /* buses                                                  */
+  int m;               /* unknowns = dim J = n_pv + 2 n_pq                         */
+  int n_pv, n_pq, n_slack;
+  int64_t nnz_ybus;
+  int64_t nnz_j;       /* structural nonzeros of J                               */
+  int64_t nnz_lu;      /* stored LU values per instance (incl. dense block pad)  */
+  int sparse_cols;     /* columns factorised by the sparse phase (first s)       */
+  int dense_dim;       /* unknowns in the trailing dense block (nd)              */
+  int dense_pad;       /* nd rounded up to the panel width                       */
+  int lu_levels;       /* level count of the sparse refactor schedule            */
+  int fwd_levels, bwd_levels;
+  double lu_fma;       /* multiply-adds of one refactorisation, one instance     */
+  double solve_fma;    /* multiply-adds of one FS/BS, one instance                */
+  int capacity;        /* batch capacity currently allocated                     */
+  int lu_precision;
+} pf_plan_info;
+
+/* Fill pf_options with the defaults (AMD ordering, FP64 LU, dense_frac 0.7,
+ * panel 8, grow-on-demand workspace). */
+int pf_options_default(pf_options* opt);
+
+/* Assemble Ybus (MATPOWER pi-model convention, Sec. 3) from branch data.
+ * host in : n buses, nbr branches, f/t [nbr] bus indices, r/x/b [nbr] series
+ *           resistance, series reactance, total line charging (p.u.).
+ * host out: rowptr [n+1], colidx [cap], y_re/y_im [cap] as CRS with sorted
+ *           columns and every diagonal present; *nnz_out = entries written.
+ * Errors: NRPF_ERR_ARG for bad sizes/indices or cap too small (then *nnz_out
+ * holds the required capacity). */
+int pf_ybus_from_branches(int n, int nbr, const int32_t* f, const int32_t* t, const double* r,
+                          const double* x, const double* b, int32_t* rowptr, int32_t* colidx,
+                          double* y_re, double* y_im, int64_t cap, int64_t* nnz_out);
+
+/* Symbolic analysis, done once per sparsity pattern (Sec. 3.2 "initialization",
+ * Sec. 4.1): bus maps, Jacobian pattern, fill-reducing ordering, LU fill,
+ * static lookup Ybus entry -> LU slots (Sec. 3.1.2), level schedules (Sec.
+ * 4.3.1); uploads everything to the current device.
+ * host in : Ybus CRS (rowptr [n+1], colidx [nnz], sorted, diagonal present,
+ *           structurally symmetric), values y_re/y_im [nnz] shared by every
+ *           instance, bus_type [n] (at least one slack).
+ * out     : *out receives a plan to be released with pf_plan_destroy.
+ * Errors: NRPF_ERR_ARG, NRPF_ERR_PATTERN, NRPF_ERR_NOMEM, NRPF_ERR_CUDA. */
+int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const double* y_re,
+                   const double* y_im, const int8_t* bus_type, const pf_options* opt,
+                   pf_plan** out);
+
+/* Sizes and work counts of a plan (host out). */
+int pf_plan_get_info(const pf_plan* p, pf_plan_info* info);
+
+/* Permutation and pattern of the factorised matrix A = P J P^T (Eq. 3).
+ * host out: pos_of_unknown [m]: position in A of J row/column u (rows and
+ *           columns share the permutation); colptr [m+1], rowidx [nnz]: CCS
+ *           pattern of L+U-I with sorted rows (the dense block listed in full);
+ *           any output pointer may be NULL.  *nnz_out = pattern size. */
+int pf_plan_get_pattern(const pf_plan* p, int32_t* pos_of_unknown, int64_t* colptr,
+                        int32_t* rowidx, int64_t* nnz_out);
+
+/* Solve B power flows (Sec. 3, steps 1-4, until max |mismatch| < tol or maxit
+ * Newton updates).
+ * device in : sbus [B,n] complex specified injections (generation - load, p.u.);
+ *             v0 [B,n] complex start; slack voltages and PV magnitudes are
+ *             held at their v0 values.
+ * device out: v_out [B,n] complex (may alias v0), iters [B] Newton updates
+ *             performed, status [B] per-instance outcome (NRPF_CONVERGED ...).
+ * stream    : cudaStream_t of the caller (NULL = legacy default stream).
+ * Asynchronous: returns after enqueueing.  Grows the workspace (device
+ * allocation, synchronous) when B exceeds the plan's capacity.
+ * Errors: NRPF_ERR_ARG (B < 0, tol not finite, maxit < 0, null pointers),
+ * NRPF_ERR_NOMEM, NRPF_ERR_CUDA.  B == 0 is a no-op. */
+int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
+                   double* v_out, int32_t* iters, uint8_t* status, void* stream);
+
+/* ---- single stages, for tests and profiling (same layouts as above) ---- */
+
+/* Alg. 1 at voltages v: F [B,m] float64 in J row order (dP of PV+PQ buses
+ * ascending, then dQ of PQ buses ascending), norm [B] = max |F|. */
+int pf_stage_mismatch(pf_plan* p, int B, const double* sbus, const double* v, double* F,
+                      double* norm, void* stream);
+
+/* Jacobian at v scattered into the permuted LU workspace (Sec. 3.1.2), then,
+ * if factor != 0, refactorised in place (Sec. 4.3).  lu_out [B, nnz] float64 in
+ * the order of pf_plan_get_pattern (CCS of A, or of L+U-I when factorised;
+ * L is unit lower and its diagonal is not stored). */
+int pf_stage_factor(pf_plan* p, int B, const double* v, int factor, double* lu_out, void* stream);
+
+/* One linear solve J(v) dx = rhs (refill, refactor, FS/BS).
+ * device in: v [B,n] complex, rhs [B,m] float64 in J row order.
+ * device out: dx [B,m] float64 in J column order. */
+int pf_stage_linear_solve(pf_plan* p, int B, const double* v, const double* rhs, double* dx,
+                          void* stream);
+
+void pf_plan_destroy(pf_plan* p);
+
+/* Static string naming a return code (or "unknown"). */
+const char* pf_status_str(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NRPF_H */
