@@ -61,6 +61,9 @@ typedef struct pf_options {
   int panel;           /* dense-block panel width (4, 8 or 16); 0 = default 8      */
   int max_batch;       /* batch capacity to allocate at plan creation; 0 = grow on
                           first solve (that call then allocates device memory)    */
+  int host_only;       /* 1: symbolic analysis only, no device memory; the plan
+                          answers pf_plan_get_info / pf_plan_get_pattern and every
+                          solve or stage call on it returns NRPF_ERR_ARG          */
 } pf_options;
 
 typedef struct pf_plan pf_plan;   /* opaque; owns its device arrays and workspace */
@@ -84,7 +87,7 @@ typedef struct pf_plan_info {
 } pf_plan_info;
 
 /* Fill pf_options with the defaults (AMD ordering, FP64 LU, dense_frac 0.7,
- * panel 8, grow-on-demand workspace). */
+ * panel 8, grow-on-demand workspace, device upload). */
 int pf_options_default(pf_options* opt);
 
 /* Assemble Ybus (MATPOWER pi-model convention, Sec. 3) from branch data.
@@ -139,8 +142,10 @@ int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, doub
 
 /* ---- single stages, for tests and profiling (same layouts as above) ---- */
 
-/* Alg. 1 at voltages v: F [B,m] float64 in J row order (dP of PV+PQ buses
- * ascending, then dQ of PQ buses ascending), norm [B] = max |F|. */
+/* Alg. 1 at voltages v: F [B,m] float64 in J row order (dP of the PV buses,
+ * then dP of the PQ buses, then dQ of the PQ buses, each group in ascending
+ * bus order; J columns follow the same order for angles and magnitudes),
+ * norm [B] = max |F|. */
 int pf_stage_mismatch(pf_plan* p, int B, const double* sbus, const double* v, double* F,
                       double* norm, void* stream);
 

@@ -1,0 +1,97 @@
+"""ctypes binding of ``libnrpf.so`` (include/nrpf.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy /
+torch objects into plain pointers and sizes.  Importing it fails loudly when
+the shared library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnrpf.so")
+
+NRPF_OK = 0
+LU_FP64, LU_FP32 = 0, 1
+ORDER_AMD, ORDER_NATURAL = 0, 1
+
+
+class NrpfError(RuntimeError):
+    pass
+
+
+class pf_options(C.Structure):
+    _fields_ = [("lu_precision", C.c_int), ("ordering", C.c_int), ("dense_frac", C.c_double),
+                ("panel", C.c_int), ("max_batch", C.c_int), ("host_only", C.c_int)]
+
+
+class pf_plan_info(C.Structure):
+    _fields_ = [("n", C.c_int), ("m", C.c_int), ("n_pv", C.c_int), ("n_pq", C.c_int),
+                ("n_slack", C.c_int), ("nnz_ybus", C.c_int64), ("nnz_j", C.c_int64),
+                ("nnz_lu", C.c_int64), ("sparse_cols", C.c_int), ("dense_dim", C.c_int),
+                ("dense_pad", C.c_int), ("lu_levels", C.c_int), ("fwd_levels", C.c_int),
+                ("bwd_levels", C.c_int), ("lu_fma", C.c_double), ("solve_fma", C.c_double),
+                ("capacity", C.c_int), ("lu_precision", C.c_int)]
+
+
+EXPORTS = ["pf_options_default", "pf_ybus_from_branches", "pf_plan_create", "pf_plan_get_info",
+           "pf_plan_get_pattern", "pf_solve_batch", "pf_stage_mismatch", "pf_stage_factor",
+           "pf_stage_linear_solve", "pf_plan_destroy", "pf_status_str"]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise NrpfError(f"{LIB_PATH} is missing: build it with "
+                        "`python -m paper_2101_02270_gb300.build` (no CPU fallback exists)")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    lib.pf_options_default.argtypes = [C.POINTER(pf_options)]
+    lib.pf_ybus_from_branches.argtypes = [I, I, P, P, P, P, P, P, P, P, P, I64, C.POINTER(I64)]
+    lib.pf_plan_create.argtypes = [I, P, P, P, P, P, C.POINTER(pf_options), C.POINTER(C.c_void_p)]
+    lib.pf_plan_get_info.argtypes = [P, C.POINTER(pf_plan_info)]
+    lib.pf_plan_get_pattern.argtypes = [P, P, P, P, C.POINTER(I64)]
+    lib.pf_solve_batch.argtypes = [P, I, P, P, D, I, P, P, P, P]
+    lib.pf_stage_mismatch.argtypes = [P, I, P, P, P, P, P]
+    lib.pf_stage_factor.argtypes = [P, I, P, I, P, P]
+    lib.pf_stage_linear_solve.argtypes = [P, I, P, P, P, P]
+    lib.pf_plan_destroy.argtypes = [P]
+    lib.pf_plan_destroy.restype = None
+    lib.pf_status_str.argtypes = [I]
+    lib.pf_status_str.restype = C.c_char_p
+    return lib
+
+
+lib = _load()
+
+
+def check(rc: int, what: str = "") -> None:
+    if rc != NRPF_OK:
+        raise NrpfError(f"{what}: {lib.pf_status_str(rc).decode()} ({rc})")
+
+
+def _np_ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data)
+
+
+def ybus_from_branches(n, f, t, r, x, b):
+    """Ybus in CRS from branch data (pi model), computed by the library on the host."""
+    f = np.ascontiguousarray(f, np.int32)
+    t = np.ascontiguousarray(t, np.int32)
+    r = np.ascontiguousarray(r, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    nbr = f.shape[0]
+    cap = n + 2 * nbr
+    rowptr = np.zeros(n + 1, np.int32)
+    colidx = np.zeros(cap, np.int32)
+    yre = np.zeros(cap)
+    yim = np.zeros(cap)
+    nnz = C.c_int64(0)
+    check(lib.pf_ybus_from_branches(n, nbr, _np_ptr(f), _np_ptr(t), _np_ptr(r), _np_ptr(x), _np_ptr(b),
+                                    _np_ptr(rowptr), _np_ptr(colidx), _np_ptr(yre), _np_ptr(yim), cap,
+                                    C.byref(nnz)), "pf_ybus_from_branches")
+    k = nnz.value
+    return rowptr, colidx[:k].copy(), yre[:k].copy(), yim[:k].copy()

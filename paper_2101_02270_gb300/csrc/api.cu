@@ -1,0 +1,451 @@
+// C ABI of the batched Newton-Raphson power-flow library (include/nrpf.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/nrpf.h"
+#include "device.h"
+#include "kernels.h"
+#include "plan.h"
+
+using nrpf::DevPlan;
+using nrpf::DevState;
+using nrpf::HostPlan;
+using nrpf::kTile;
+
+struct pf_plan {
+  HostPlan hp;
+  DevPlan dp{};
+  DevState st{};
+  int capacity = 0;  // instances (multiple of kTile)
+  int lu_precision = NRPF_LU_FP64;
+  int device = 0;
+  int host_only = 0;
+  std::vector<void*> plan_allocs;
+  std::vector<void*> ws_allocs;
+  int64_t* d_pattern_map = nullptr;  // CCS pattern -> LU element
+  int64_t pattern_nnz = 0;
+  std::string last_error;
+};
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) {                       \
+      return e_ == cudaErrorMemoryAllocation ? NRPF_ERR_NOMEM : NRPF_ERR_CUDA; \
+    }                                              \
+  } while (0)
+
+template <typename T>
+int upload(pf_plan* p, const std::vector<T>& v, const T** out) {
+  if (v.empty()) { *out = nullptr; return NRPF_OK; }
+  void* d = nullptr;
+  CK(cudaMalloc(&d, v.size() * sizeof(T)));
+  p->plan_allocs.push_back(d);
+  CK(cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = reinterpret_cast<const T*>(d);
+  return NRPF_OK;
+}
+
+void free_ws(pf_plan* p) {
+  for (void* a : p->ws_allocs) cudaFree(a);
+  p->ws_allocs.clear();
+  p->capacity = 0;
+  p->st = DevState{};
+}
+
+int ensure_capacity(pf_plan* p, int B) {
+  const int Bp = (B + kTile - 1) / kTile * kTile;
+  if (Bp <= p->capacity) return NRPF_OK;
+  // The new workspace replaces the old one: wait for work still using it.
+  CK(cudaDeviceSynchronize());
+  free_ws(p);
+  const HostPlan& h = p->hp;
+  const size_t w = p->lu_precision == NRPF_LU_FP32 ? 4 : 8;
+  auto alloc = [&](size_t bytes, void** out) -> int {
+    void* d = nullptr;
+    CK(cudaMalloc(&d, std::max<size_t>(bytes, 256)));
+    p->ws_allocs.push_back(d);
+    *out = d;
+    return NRPF_OK;
+  };
+  DevState s{};
+  s.Bp = Bp;
+  int rc = NRPF_OK;
+  const size_t nb = (size_t)h.n * Bp * sizeof(double);
+  void* t = nullptr;
+#define AL(bytes, field, type)            \
+  if ((rc = alloc((bytes), &t))) { free_ws(p); return rc; } \
+  s.field = reinterpret_cast<type>(t);
+  AL(nb, vm, double*);
+  AL(nb, va, double*);
+  AL(nb, ve, double*);
+  AL(nb, vf, double*);
+  AL(nb, vinv, double*);
+  AL(nb, psp, double*);
+  AL(nb, qsp, double*);
+  AL((size_t)(h.s + h.ndp) * Bp * w, x, void*);
+  AL((size_t)h.NLU * Bp * w, lu, void*);
+  AL((size_t)std::max(h.kb, 1) * Bp * w, inv, void*);
+  AL((size_t)Bp * sizeof(unsigned long long), norm, unsigned long long*);
+  AL((size_t)Bp * 4, iters, int32_t*);
+  AL((size_t)Bp * 4, status, int32_t*);
+  AL((size_t)Bp * 4, active, int32_t*);
+  AL((size_t)Bp * 4, bad, int32_t*);
+  AL(2 * 4, n_active, int32_t*);
+#undef AL
+  p->st = s;
+  p->capacity = Bp;
+  return NRPF_OK;
+}
+
+template <typename T>
+void enqueue_solve(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
+                   double* v_out, int32_t* iters, uint8_t* status, cudaStream_t st) {
+  const DevPlan& P = p->dp;
+  const DevState& S = p->st;
+  const HostPlan& h = p->hp;
+  nrpf::launch_load(P, S, B, sbus, v0, st);
+  cudaMemsetAsync(S.n_active, 0, 2 * sizeof(int32_t), st);
+  for (int it = 0; it <= maxit; ++it) {
+    int32_t* counter = S.n_active + (it & 1);
+    const int32_t* prev = it == 0 ? nullptr : S.n_active + ((it - 1) & 1);
+    if (P.m > 0) {
+      nrpf::launch_prepare_lu<T>(P, S, prev, st);
+      nrpf::launch_mismatch<T>(P, S, 1, prev, st);
+    }
+    cudaMemsetAsync(counter, 0, sizeof(int32_t), st);
+    nrpf::launch_check(S, it, maxit, tol, counter, st);
+    if (it == maxit || P.m == 0) break;
+    nrpf::launch_factor<T>(P, S, h.lu_lvl_ptr, counter, st);
+    nrpf::launch_solve<T>(P, S, h.fw_lvl_ptr, h.bw_lvl_ptr, counter, st);
+    nrpf::launch_update<T>(P, S, counter, st);
+  }
+  nrpf::launch_store(P, S, B, v_out, iters, status, st);
+}
+
+int build_pattern_map(pf_plan* p) {
+  if (p->d_pattern_map) return NRPF_OK;
+  const HostPlan& h = p->hp;
+  std::vector<int64_t> map;
+  map.reserve((size_t)h.nnz_pattern);
+  for (int j = 0; j < h.m; ++j) {
+    for (int64_t q = h.cs[j]; q < h.ce[j]; ++q) map.push_back(q);
+    if (j >= h.s)
+      for (int r = h.s; r < h.m; ++r) map.push_back(h.NS + (int64_t)(j - h.s) * h.ndp + (r - h.s));
+  }
+  p->pattern_nnz = (int64_t)map.size();
+  if (map.empty()) return NRPF_OK;
+  void* d = nullptr;
+  CK(cudaMalloc(&d, map.size() * sizeof(int64_t)));
+  CK(cudaMemcpy(d, map.data(), map.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  p->d_pattern_map = reinterpret_cast<int64_t*>(d);
+  return NRPF_OK;
+}
+
+template <typename T>
+void enqueue_factor(pf_plan* p, int factor, cudaStream_t st) {
+  nrpf::launch_prepare_lu<T>(p->dp, p->st, nullptr, st);
+  nrpf::launch_mismatch<T>(p->dp, p->st, 1, nullptr, st);
+  if (factor) nrpf::launch_factor<T>(p->dp, p->st, p->hp.lu_lvl_ptr, nullptr, st);
+}
+
+int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return NRPF_OK;
+  return e == cudaErrorMemoryAllocation ? NRPF_ERR_NOMEM : NRPF_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pf_options_default(pf_options* opt) {
+  if (!opt) return NRPF_ERR_ARG;
+  opt->lu_precision = NRPF_LU_FP64;
+  opt->ordering = NRPF_ORDER_AMD;
+  opt->dense_frac = 0.7;
+  opt->panel = 8;
+  opt->max_batch = 0;
+  opt->host_only = 0;
+  return NRPF_OK;
+}
+
+int pf_ybus_from_branches(int n, int nbr, const int32_t* f, const int32_t* t, const double* r,
+                          const double* x, const double* b, int32_t* rowptr, int32_t* colidx,
+                          double* y_re, double* y_im, int64_t cap, int64_t* nnz_out) {
+  if (n <= 0 || nbr < 0 || !rowptr || !nnz_out) return NRPF_ERR_ARG;
+  if (nbr > 0 && (!f || !t || !r || !x || !b)) return NRPF_ERR_ARG;
+  // pi model: ys = 1/(r + jx); Y_ff += ys + jb/2, Y_tt += ys + jb/2, Y_ft -= ys, Y_tf -= ys
+  std::vector<std::map<int, std::pair<double, double>>> rows(n);
+  for (int i = 0; i < n; ++i) rows[i][i] = {0.0, 0.0};
+  for (int e = 0; e < nbr; ++e) {
+    const int a = f[e], c = t[e];
+    if (a < 0 || a >= n || c < 0 || c >= n) return NRPF_ERR_ARG;
+    const double den = r[e] * r[e] + x[e] * x[e];
+    if (!(den > 0.0) || !std::isfinite(den) || !std::isfinite(b[e])) return NRPF_ERR_ARG;
+    const double gs = r[e] / den, bs = -x[e] / den;
+    auto add = [&](int i, int k, double gr, double gi) {
+      auto& v = rows[i][k];
+      v.first += gr;
+      v.second += gi;
+    };
+    add(a, a, gs, bs + 0.5 * b[e]);
+    add(c, c, gs, bs + 0.5 * b[e]);
+    add(a, c, -gs, -bs);
+    add(c, a, -gs, -bs);
+  }
+  int64_t nnz = 0;
+  for (auto& row : rows) nnz += (int64_t)row.size();
+  *nnz_out = nnz;
+  if (nnz > cap || !colidx || !y_re || !y_im) return NRPF_ERR_ARG;
+  int64_t q = 0;
+  rowptr[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    for (auto& kv : rows[i]) {
+      colidx[q] = kv.first;
+      y_re[q] = kv.second.first;
+      y_im[q] = kv.second.second;
+      ++q;
+    }
+    rowptr[i + 1] = (int32_t)q;
+  }
+  return NRPF_OK;
+}
+
+int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const double* y_re,
+                   const double* y_im, const int8_t* bus_type, const pf_options* opt, pf_plan** out) {
+  if (!out) return NRPF_ERR_ARG;
+  *out = nullptr;
+  pf_options o;
+  pf_options_default(&o);
+  if (opt) {
+    o = *opt;
+    if (o.dense_frac == 0.0) o.dense_frac = 0.7;
+    if (o.panel == 0) o.panel = 8;
+  }
+  if (o.lu_precision != NRPF_LU_FP64 && o.lu_precision != NRPF_LU_FP32) return NRPF_ERR_ARG;
+  if (o.ordering != NRPF_ORDER_AMD && o.ordering != NRPF_ORDER_NATURAL) return NRPF_ERR_ARG;
+  if (!(o.dense_frac > 0.0) || o.max_batch < 0) return NRPF_ERR_ARG;
+  pf_plan* p = new (std::nothrow) pf_plan();
+  if (!p) return NRPF_ERR_NOMEM;
+  std::string err;
+  int rc;
+  try {
+    rc = nrpf::build_plan(n, rowptr, colidx, y_re, y_im, bus_type, o.ordering, o.dense_frac, o.panel,
+                          p->hp, err);
+  } catch (const std::bad_alloc&) {
+    rc = NRPF_ERR_NOMEM;
+  } catch (...) {
+    rc = NRPF_ERR_ARG;
+  }
+  if (rc) {
+    delete p;
+    return rc;
+  }
+  p->lu_precision = o.lu_precision;
+  p->host_only = o.host_only != 0;
+  if (p->host_only) {
+    *out = p;
+    return NRPF_OK;
+  }
+  cudaGetDevice(&p->device);
+  const HostPlan& h = p->hp;
+  DevPlan& d = p->dp;
+  d.n = h.n; d.m = h.m; d.s = h.s; d.nd = h.nd; d.ndp = h.ndp; d.kb = h.kb; d.mp = h.s + h.ndp;
+  d.NS = h.NS; d.NLU = h.NLU; d.nnzY = (int)h.colidx.size();
+  d.n_one = (int)h.one_pos.size();
+  std::vector<int32_t> ydiag(h.n);
+  for (int i = 0; i < h.n; ++i)
+    for (int q = h.rowptr[i]; q < h.rowptr[i + 1]; ++q)
+      if (h.colidx[q] == i) ydiag[i] = q;
+  std::vector<nrpf::DevUpd> upd(h.upd.size());
+  for (size_t u = 0; u < h.upd.size(); ++u)
+    upd[u] = nrpf::DevUpd{h.upd[u].ukj, h.upd[u].lsrc, h.upd[u].llen, h.upd[u].dst_off};
+  if ((rc = upload(p, h.rowptr, &d.rowptr)) || (rc = upload(p, h.colidx, &d.colidx)) ||
+      (rc = upload(p, h.yre, &d.yre)) || (rc = upload(p, h.yim, &d.yim)) ||
+      (rc = upload(p, ydiag, &d.ydiag)) || (rc = upload(p, h.bus_type, &d.bus_type)) ||
+      (rc = upload(p, h.jmap, &d.jmap)) || (rc = upload(p, h.rhs_pos_p, &d.rhs_p)) ||
+      (rc = upload(p, h.rhs_pos_q, &d.rhs_q)) || (rc = upload(p, h.one_pos, &d.one_pos)) ||
+      (rc = upload(p, h.lu_lvl_cols, &d.lu_cols)) || (rc = upload(p, h.col_upd_ptr, &d.col_upd_ptr)) ||
+      (rc = upload(p, upd, &d.upd)) || (rc = upload(p, h.dst, &d.dst)) || (rc = upload(p, h.dp, &d.dp)) ||
+      (rc = upload(p, h.ce, &d.ce)) || (rc = upload(p, h.fw_rows, &d.fw_rows)) ||
+      (rc = upload(p, h.fw_ptr, &d.fw_ptr)) || (rc = upload(p, h.fw_pos, &d.fw_pos)) ||
+      (rc = upload(p, h.fw_col, &d.fw_col)) || (rc = upload(p, h.bw_rows, &d.bw_rows)) ||
+      (rc = upload(p, h.bw_ptr, &d.bw_ptr)) || (rc = upload(p, h.bw_pos, &d.bw_pos)) ||
+      (rc = upload(p, h.bw_col, &d.bw_col)) || (rc = upload(p, h.unk_pos, &d.unk_pos))) {
+    pf_plan_destroy(p);
+    return rc;
+  }
+  if (o.max_batch > 0 && (rc = ensure_capacity(p, o.max_batch))) {
+    pf_plan_destroy(p);
+    return rc;
+  }
+  *out = p;
+  return NRPF_OK;
+}
+
+int pf_plan_get_info(const pf_plan* p, pf_plan_info* info) {
+  if (!p || !info) return NRPF_ERR_ARG;
+  const HostPlan& h = p->hp;
+  info->n = h.n;
+  info->m = h.m;
+  info->n_pv = h.npv;
+  info->n_pq = h.npq;
+  info->n_slack = h.nslack;
+  info->nnz_ybus = (int64_t)h.colidx.size();
+  info->nnz_j = h.nnz_j;
+  info->nnz_lu = h.NLU;
+  info->sparse_cols = h.s;
+  info->dense_dim = h.nd;
+  info->dense_pad = h.ndp;
+  info->lu_levels = (int)h.lu_lvl_ptr.size() - 1;
+  info->fwd_levels = (int)h.fw_lvl_ptr.size() - 1;
+  info->bwd_levels = (int)h.bw_lvl_ptr.size() - 1;
+  info->lu_fma = h.lu_fma;
+  info->solve_fma = h.solve_fma;
+  info->capacity = p->capacity;
+  info->lu_precision = p->lu_precision;
+  return NRPF_OK;
+}
+
+int pf_plan_get_pattern(const pf_plan* p, int32_t* pos_of_unknown, int64_t* colptr, int32_t* rowidx,
+                        int64_t* nnz_out) {
+  if (!p) return NRPF_ERR_ARG;
+  const HostPlan& h = p->hp;
+  if (pos_of_unknown) std::copy(h.unk_pos.begin(), h.unk_pos.end(), pos_of_unknown);
+  int64_t q = 0;
+  if (colptr) colptr[0] = 0;
+  for (int j = 0; j < h.m; ++j) {
+    for (int64_t e = h.cs[j]; e < h.ce[j]; ++e) {
+      if (rowidx) rowidx[q] = h.seg_row[e];
+      ++q;
+    }
+    if (j >= h.s)
+      for (int r = h.s; r < h.m; ++r) {
+        if (rowidx) rowidx[q] = r;
+        ++q;
+      }
+    if (colptr) colptr[j + 1] = q;
+  }
+  if (nnz_out) *nnz_out = q;
+  return NRPF_OK;
+}
+
+int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
+                   double* v_out, int32_t* iters, uint8_t* status, void* stream) {
+  if (!p || p->host_only || B < 0 || maxit < 0 || !std::isfinite(tol) || tol < 0) return NRPF_ERR_ARG;
+  if (B == 0) return NRPF_OK;
+  if (!sbus || !v0 || !v_out || !iters || !status) return NRPF_ERR_ARG;
+  int rc = ensure_capacity(p, B);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (p->lu_precision == NRPF_LU_FP32)
+    enqueue_solve<float>(p, B, sbus, v0, tol, maxit, v_out, iters, status, st);
+  else
+    enqueue_solve<double>(p, B, sbus, v0, tol, maxit, v_out, iters, status, st);
+  return check_launch();
+}
+
+int pf_stage_mismatch(pf_plan* p, int B, const double* sbus, const double* v, double* F, double* norm,
+                      void* stream) {
+  if (!p || p->host_only || B < 0) return NRPF_ERR_ARG;
+  if (B == 0) return NRPF_OK;
+  if (!sbus || !v || !F || !norm) return NRPF_ERR_ARG;
+  int rc = ensure_capacity(p, B);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  nrpf::launch_load(p->dp, p->st, B, sbus, v, st);
+  if (p->lu_precision == NRPF_LU_FP32) {
+    nrpf::launch_mismatch<float>(p->dp, p->st, 0, nullptr, st);
+    nrpf::launch_f_out<float>(p->dp, p->st, B, F, norm, st);
+  } else {
+    nrpf::launch_mismatch<double>(p->dp, p->st, 0, nullptr, st);
+    nrpf::launch_f_out<double>(p->dp, p->st, B, F, norm, st);
+  }
+  return check_launch();
+}
+
+int pf_stage_factor(pf_plan* p, int B, const double* v, int factor, double* lu_out, void* stream) {
+  if (!p || p->host_only || B < 0) return NRPF_ERR_ARG;
+  if (B == 0) return NRPF_OK;
+  if (!v || !lu_out) return NRPF_ERR_ARG;
+  int rc = ensure_capacity(p, B);
+  if (rc) return rc;
+  if ((rc = build_pattern_map(p))) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the specified injections do not enter J: reuse v as a harmless sbus
+  nrpf::launch_load(p->dp, p->st, B, v, v, st);
+  if (p->hp.m == 0) return check_launch();
+  if (p->lu_precision == NRPF_LU_FP32) {
+    enqueue_factor<float>(p, factor, st);
+    nrpf::launch_lu_out<float>(p->dp, p->st, B, p->d_pattern_map, p->pattern_nnz, lu_out, st);
+  } else {
+    enqueue_factor<double>(p, factor, st);
+    nrpf::launch_lu_out<double>(p->dp, p->st, B, p->d_pattern_map, p->pattern_nnz, lu_out, st);
+  }
+  return check_launch();
+}
+
+int pf_stage_linear_solve(pf_plan* p, int B, const double* v, const double* rhs, double* dx, void* stream) {
+  if (!p || p->host_only || B < 0) return NRPF_ERR_ARG;
+  if (B == 0) return NRPF_OK;
+  if (!v || !rhs || !dx) return NRPF_ERR_ARG;
+  int rc = ensure_capacity(p, B);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  nrpf::launch_load(p->dp, p->st, B, v, v, st);
+  if (p->hp.m == 0) return check_launch();
+  if (p->lu_precision == NRPF_LU_FP32) {
+    enqueue_factor<float>(p, 1, st);
+    nrpf::launch_rhs_in<float>(p->dp, p->st, B, rhs, st);
+    nrpf::launch_solve<float>(p->dp, p->st, p->hp.fw_lvl_ptr, p->hp.bw_lvl_ptr, nullptr, st);
+    nrpf::launch_rhs_out<float>(p->dp, p->st, B, dx, st);
+  } else {
+    enqueue_factor<double>(p, 1, st);
+    nrpf::launch_rhs_in<double>(p->dp, p->st, B, rhs, st);
+    nrpf::launch_solve<double>(p->dp, p->st, p->hp.fw_lvl_ptr, p->hp.bw_lvl_ptr, nullptr, st);
+    nrpf::launch_rhs_out<double>(p->dp, p->st, B, dx, st);
+  }
+  return check_launch();
+}
+
+void pf_plan_destroy(pf_plan* p) {
+  if (!p) return;
+  if (p->host_only) {
+    delete p;
+    return;
+  }
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != p->device) cudaSetDevice(p->device);
+  cudaDeviceSynchronize();
+  free_ws(p);
+  for (void* a : p->plan_allocs) cudaFree(a);
+  if (p->d_pattern_map) cudaFree(p->d_pattern_map);
+  if (cur != p->device) cudaSetDevice(cur);
+  delete p;
+}
+
+const char* pf_status_str(int code) {
+  switch (code) {
+    case NRPF_OK: return "ok";
+    case NRPF_ERR_ARG: return "invalid argument";
+    case NRPF_ERR_PATTERN: return "invalid Ybus pattern or bus types";
+    case NRPF_ERR_NOMEM: return "out of memory";
+    case NRPF_ERR_CUDA: return "CUDA runtime error";
+    case NRPF_ERR_CAPACITY: return "batch exceeds plan capacity";
+    default: return "unknown";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,727 @@
+// Batched Newton-Raphson kernels (sm_103a).  Every kernel works on tiles of
+// kTile = 32 interleaved instances: lane = instance within the tile, so all
+// plan indices are warp-uniform (broadcast loads) and all value accesses are
+// contiguous across the warp.
+#include <cfloat>
+#include <cstdint>
+#include <vector>
+
+#include "device.h"
+#include "kernels.h"
+
+namespace nrpf {
+
+namespace {
+
+__device__ __forceinline__ size_t sidx(int tile, int64_t E, int64_t e, int lane) {
+  return ((size_t)tile * (size_t)E + (size_t)e) * kTile + lane;
+}
+
+__device__ __forceinline__ bool tile_active(const DevState& S, int tile, int lane) {
+  return __any_sync(0xffffffffu, S.active[tile * kTile + lane] != 0);
+}
+
+// ---------------------------------------------------------------------------
+// Input / output transposes: user [B, n] complex128 <-> interleaved tiles
+// (the paper's "transpose to batch" step on the device, Sec. 3.2).
+// Block (32, 8): a 32-bus x 32-instance tile through shared memory.
+// ---------------------------------------------------------------------------
+__global__ void k_load(DevPlan P, DevState S, int B, const double2* __restrict__ sbus,
+                       const double2* __restrict__ v0) {
+  __shared__ double2 ss[32][33];
+  __shared__ double2 sv[32][33];
+  const int tile = blockIdx.y;
+  const int i0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int r = ty; r < 32; r += 8) {
+    int b = tile * kTile + r;
+    int i = i0 + tx;
+    double2 s = make_double2(0.0, 0.0), v = make_double2(1.0, 0.0);
+    if (b < B && i < P.n) {
+      s = sbus[(size_t)b * P.n + i];
+      v = v0[(size_t)b * P.n + i];
+    }
+    ss[r][tx] = s;
+    sv[r][tx] = v;
+  }
+  __syncthreads();
+  for (int c = ty; c < 32; c += 8) {
+    int i = i0 + c;
+    if (i >= P.n) continue;
+    double2 s = ss[tx][c], v = sv[tx][c];
+    size_t o = sidx(tile, P.n, i, tx);
+    double vm = sqrt(v.x * v.x + v.y * v.y);
+    S.psp[o] = s.x;
+    S.qsp[o] = s.y;
+    S.vm[o] = vm;
+    S.va[o] = atan2(v.y, v.x);
+    S.ve[o] = v.x;
+    S.vf[o] = v.y;
+    S.vinv[o] = 1.0 / vm;
+  }
+  if (blockIdx.x == 0 && ty == 0) {
+    int b = tile * kTile + tx;
+    S.iters[b] = 0;
+    S.status[b] = NRPF_MAXIT_CODE;
+    S.active[b] = b < B ? 1 : 0;
+    S.bad[b] = 0;
+    S.norm[b] = 0ull;
+  }
+}
+
+__global__ void k_store(DevPlan P, DevState S, int B, double2* __restrict__ v_out,
+                        int32_t* __restrict__ iters, uint8_t* __restrict__ status) {
+  __shared__ double2 sv[32][33];
+  const int tile = blockIdx.y;
+  const int i0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int c = ty; c < 32; c += 8) {
+    int i = i0 + c;
+    if (i >= P.n) continue;
+    size_t o = sidx(tile, P.n, i, tx);
+    sv[tx][c] = make_double2(S.ve[o], S.vf[o]);
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    int b = tile * kTile + r;
+    int i = i0 + tx;
+    if (b < B && i < P.n) v_out[(size_t)b * P.n + i] = sv[r][tx];
+  }
+  if (blockIdx.x == 0 && ty == 0) {
+    int b = tile * kTile + tx;
+    if (b < B) {
+      iters[b] = S.iters[b];
+      status[b] = (uint8_t)S.status[b];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Nodal power mismatch (Eq. 1, Alg. 1) fused with the Jacobian refill straight
+// into the permuted LU workspace (Sec. 3.1.2, static lookup jmap).
+// Rectangular voltages e + jf avoid a sine/cosine per admittance entry:
+//   I_i = sum_k Y_ik V_k,  S_i = V_i conj(I_i)
+//   W_ik = V_i conj(Y_ik V_k)          (k != i)
+//   dP_i/dth_k = Im W_ik, dQ_i/dth_k = -Re W_ik,
+//   dP_i/d|V_k| = Re W_ik / |V_k|, dQ_i/d|V_k| = Im W_ik / |V_k|
+//   dP_i/dth_i = -Q_i - B_ii |V_i|^2,  dQ_i/dth_i = P_i - G_ii |V_i|^2
+//   dP_i/d|V_i| = P_i/|V_i| + G_ii |V_i|, dQ_i/d|V_i| = Q_i/|V_i| - B_ii |V_i|
+// Block: 32 lanes x kWarps warps; each warp walks kBusPerWarp buses.
+// The right-hand side receives -F at the permuted row of each equation.
+// ---------------------------------------------------------------------------
+constexpr int kMWarps = 8;
+constexpr int kBusPerWarp = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevState S, int jac,
+                                                               const int32_t* __restrict__ gate) {
+  __shared__ double red[kMWarps][32];
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int tile = blockIdx.y;
+  if (gate && *gate == 0) return;
+  T* __restrict__ LU = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;
+  T* __restrict__ X = reinterpret_cast<T*>(S.x) + (size_t)tile * P.mp * kTile;
+  const double* __restrict__ ve = S.ve + (size_t)tile * P.n * kTile;
+  const double* __restrict__ vf = S.vf + (size_t)tile * P.n * kTile;
+  const double* __restrict__ vinv = S.vinv + (size_t)tile * P.n * kTile;
+  double nrm = 0.0;
+  const int ibeg = (blockIdx.x * kMWarps + warp) * kBusPerWarp;
+  for (int ii = 0; ii < kBusPerWarp; ++ii) {
+    const int i = ibeg + ii;
+    if (i >= P.n) break;
+    const int bt = P.bus_type[i];
+    if (bt == 3) continue;
+    const double ei = ve[i * kTile + lane], fi = vf[i * kTile + lane];
+    double Ir = 0.0, Ii = 0.0;
+    const int d0 = P.rowptr[i], d1 = P.rowptr[i + 1];
+    for (int d = d0; d < d1; ++d) {
+      const int k = P.colidx[d];
+      const double G = P.yre[d], Bv = P.yim[d];
+      const double ek = ve[k * kTile + lane], fk = vf[k * kTile + lane];
+      const double yr = G * ek - Bv * fk;
+      const double yi = G * fk + Bv * ek;
+      Ir += yr;
+      Ii += yi;
+      if (jac && k != i) {
+        const int4 jm = reinterpret_cast<const int4*>(P.jmap)[d];
+        if (jm.x >= 0) {
+          const double Wr = ei * yr + fi * yi;
+          const double Wi = fi * yr - ei * yi;
+          const double ik = vinv[k * kTile + lane];
+          LU[(size_t)jm.x * kTile + lane] = (T)Wi;
+          if (jm.y >= 0) LU[(size_t)jm.y * kTile + lane] = (T)(Wr * ik);
+          if (jm.z >= 0) LU[(size_t)jm.z * kTile + lane] = (T)(-Wr);
+          if (jm.w >= 0) LU[(size_t)jm.w * kTile + lane] = (T)(Wi * ik);
+        }
+      }
+    }
+    const double Pc = ei * Ir + fi * Ii;
+    const double Qc = fi * Ir - ei * Ii;
+    const size_t o = (size_t)i * kTile + lane;
+    const size_t so = (size_t)tile * P.n * kTile + o;
+    const double dP = Pc - S.psp[so];
+    double a = fabs(dP);
+    X[(size_t)P.rhs_p[i] * kTile + lane] = (T)(-dP);
+    if (bt == 1) {
+      const double dQ = Qc - S.qsp[so];
+      X[(size_t)P.rhs_q[i] * kTile + lane] = (T)(-dQ);
+      const double q = fabs(dQ);
+      a = (q > a || q != q) ? q : a;
+    }
+    nrm = (a > nrm || a != a) ? a : nrm;
+    if (jac) {
+      const int dd = P.ydiag[i];
+      const int4 jm = reinterpret_cast<const int4*>(P.jmap)[dd];
+      const double G = P.yre[dd], Bv = P.yim[dd];
+      const double vm2 = ei * ei + fi * fi;
+      const double ivm = vinv[o];
+      const double vm = vm2 * ivm;
+      LU[(size_t)jm.x * kTile + lane] = (T)(-Qc - Bv * vm2);
+      if (jm.y >= 0) LU[(size_t)jm.y * kTile + lane] = (T)(Pc * ivm + G * vm);
+      if (jm.z >= 0) LU[(size_t)jm.z * kTile + lane] = (T)(Pc - G * vm2);
+      if (jm.w >= 0) LU[(size_t)jm.w * kTile + lane] = (T)(Qc * ivm - Bv * vm);
+    }
+  }
+  // NaN -> +inf so that the unsigned-integer max keeps it
+  if (!(nrm <= DBL_MAX)) nrm = __longlong_as_double(0x7ff0000000000000ll);
+  red[warp][lane] = nrm;
+  __syncthreads();
+  if (warp == 0) {
+    double r = red[0][lane];
+    for (int w = 1; w < kMWarps; ++w) r = fmax(r, red[w][lane]);
+    atomicMax(&S.norm[tile * kTile + lane], (unsigned long long)__double_as_longlong(r));
+  }
+}
+
+// Convergence test and per-instance bookkeeping, one thread per instance.
+// it = number of updates performed so far.
+__global__ void k_check(DevState S, int Bp, int it, int maxit, double tol, int32_t* counter) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= Bp) return;
+  const double nrm = __longlong_as_double((long long)S.norm[b]);
+  S.norm[b] = 0ull;
+  if (!S.active[b]) return;
+  int keep = 0;
+  if (S.bad[b]) {  // the previous step was not finite: it does not count
+    S.status[b] = NRPF_FAILED_CODE;
+    S.iters[b] = it - 1;
+  } else if (!(nrm <= DBL_MAX)) {
+    S.status[b] = NRPF_FAILED_CODE;
+    S.iters[b] = it;
+  } else if (nrm < tol) {
+    S.status[b] = NRPF_CONVERGED_CODE;
+    S.iters[b] = it;
+  } else if (it >= maxit) {
+    S.status[b] = NRPF_MAXIT_CODE;
+    S.iters[b] = it;
+  } else {
+    keep = 1;
+    S.iters[b] = it + 1;
+  }
+  S.active[b] = keep;
+  const unsigned mask = __ballot_sync(__activemask(), keep);
+  if (keep && (threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(counter, __popc(mask));
+}
+
+// Zero a buffer (16-byte stores, grid-stride), skipped once no instance is
+// active.
+__global__ void k_zero16(uint4* __restrict__ p, size_t n16, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
+    p[i] = z;
+}
+
+// Identity on the padding of the dense block.
+template <typename T>
+__global__ void k_set_ones(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int tile = blockIdx.y, lane = threadIdx.x;
+  T* LU = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;
+  for (int t = threadIdx.y; t < P.n_one; t += blockDim.y) LU[(size_t)P.one_pos[t] * kTile + lane] = (T)1;
+}
+
+// ---------------------------------------------------------------------------
+// Sparse left-looking refactorisation, one level of the column schedule
+// (Alg. 2 / Alg. 3 stage 1: every column of a level in parallel, one lane per
+// instance).  Column j: for each finished column k with U(k,j) != 0, in
+// ascending k:  col_j[rows of L(:,k)] -= U(k,j) * L(:,k);  then, for a sparse
+// column, L(:,j) /= U(j,j).  Dense-block columns only receive the updates of
+// the sparse columns (their Schur complement), and are finished later.
+// ---------------------------------------------------------------------------
+constexpr int kLWarps = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, DevState S, int c0, int c1,
+                                                                  const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int lane = threadIdx.x;
+  const int ci = c0 + blockIdx.x * kLWarps + threadIdx.y;
+  const int tile = blockIdx.y;
+  if (ci >= c1) return;
+  if (!tile_active(S, tile, lane)) return;
+  T* __restrict__ LU = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile + lane;
+  const int j = P.lu_cols[ci];
+  const int u0 = P.col_upd_ptr[j], u1 = P.col_upd_ptr[j + 1];
+  for (int u = u0; u < u1; ++u) {
+    const DevUpd up = P.upd[u];
+    const T x = LU[(size_t)up.ukj * kTile];
+    const int32_t* __restrict__ dst = P.dst + up.dst_off;
+    const T* __restrict__ src = LU + (size_t)up.lsrc * kTile;
+    int q = 0;
+    for (; q + 4 <= up.llen; q += 4) {
+      const int d0 = dst[q], d1 = dst[q + 1], d2 = dst[q + 2], d3 = dst[q + 3];
+      const T s0 = src[(size_t)q * kTile], s1 = src[(size_t)(q + 1) * kTile];
+      const T s2 = src[(size_t)(q + 2) * kTile], s3 = src[(size_t)(q + 3) * kTile];
+      const T a0 = LU[(size_t)d0 * kTile], a1 = LU[(size_t)d1 * kTile];
+      const T a2 = LU[(size_t)d2 * kTile], a3 = LU[(size_t)d3 * kTile];
+      LU[(size_t)d0 * kTile] = a0 - x * s0;
+      LU[(size_t)d1 * kTile] = a1 - x * s1;
+      LU[(size_t)d2 * kTile] = a2 - x * s2;
+      LU[(size_t)d3 * kTile] = a3 - x * s3;
+    }
+    for (; q < up.llen; ++q) {
+      const int d = dst[q];
+      LU[(size_t)d * kTile] -= x * src[(size_t)q * kTile];
+    }
+  }
+  const int dpj = P.dp[j];
+  if (dpj >= 0) {
+    const T inv = (T)1 / LU[(size_t)dpj * kTile];
+    const int64_t e = P.ce[j];
+    for (int64_t p = dpj + 1; p < e; ++p) LU[(size_t)p * kTile] *= inv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense trailing block: right-looking blocked LU without pivoting, panel width
+// kb, on every instance's ndp x ndp column-major block (Sec. 4.3: the serial
+// tail of the column DAG, where few columns remain per level, is handled as
+// one dense matrix whose updates are independent multiply-adds).
+//   (a) k_dense_diag   : factor the kb x kb diagonal block, store 1/pivots
+//   (b) k_dense_panel  : L21 = A21 U11^-1 (rows) and U12 = L11^-1 A12 (cols),
+//                        four rows or four columns per thread
+//   (c) k_dense_update : A22 -= L21 U12, a 4 x 4 register tile per thread
+// ---------------------------------------------------------------------------
+template <typename T, int KB>
+__global__ void k_dense_diag(DevPlan P, DevState S, int k, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int lane = threadIdx.x;
+  const int tile = blockIdx.x * blockDim.y + threadIdx.y;
+  if (tile * kTile >= S.Bp) return;
+  if (!tile_active(S, tile, lane)) return;
+  T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
+  T* __restrict__ inv = reinterpret_cast<T*>(S.inv) + (size_t)tile * KB * kTile + lane;
+  const int ld = P.ndp;
+  T D[KB][KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c)
+#pragma unroll
+    for (int r = 0; r < KB; ++r) D[r][c] = A[((size_t)(k + c) * ld + (k + r)) * kTile];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) {
+    const T ip = (T)1 / D[c][c];
+    inv[c * kTile] = ip;
+#pragma unroll
+    for (int r = c + 1; r < KB; ++r) D[r][c] *= ip;
+#pragma unroll
+    for (int cc = c + 1; cc < KB; ++cc)
+#pragma unroll
+      for (int r = c + 1; r < KB; ++r) D[r][cc] -= D[r][c] * D[c][cc];
+  }
+#pragma unroll
+  for (int c = 0; c < KB; ++c)
+#pragma unroll
+    for (int r = 0; r < KB; ++r) A[((size_t)(k + c) * ld + (k + r)) * kTile] = D[r][c];
+}
+
+template <typename T, int KB>
+__global__ void k_dense_panel(DevPlan P, DevState S, int k, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int lane = threadIdx.x;
+  const int tile = blockIdx.y;
+  if (!tile_active(S, tile, lane)) return;
+  const int ld = P.ndp;
+  const int r0 = k + KB;            // first trailing row/column
+  const int ngrp = (ld - r0) / 4;   // groups of four rows (and of four columns)
+  const int g = blockIdx.x * blockDim.y + threadIdx.y;
+  if (g >= 2 * ngrp) return;
+  T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
+  const T* __restrict__ inv = reinterpret_cast<const T*>(S.inv) + (size_t)tile * KB * kTile + lane;
+  auto at = [&](int r, int c) -> T& { return A[((size_t)c * ld + r) * kTile]; };
+  if (g < ngrp) {
+    // rows i0..i0+3: x U11 = a  (U11 upper, pivots inverted)
+    const int i0 = r0 + 4 * g;
+    T x[4][KB];
+#pragma unroll
+    for (int c = 0; c < KB; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) x[t][c] = at(i0 + t, k + c);
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+#pragma unroll
+      for (int p = 0; p < c; ++p) {
+        const T u = at(k + p, k + c);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) x[t][c] -= x[t][p] * u;
+      }
+      const T ip = inv[c * kTile];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) x[t][c] *= ip;
+    }
+#pragma unroll
+    for (int c = 0; c < KB; ++c)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) at(i0 + t, k + c) = x[t][c];
+  } else {
+    // columns j0..j0+3: L11 y = a  (L11 unit lower)
+    const int j0 = r0 + 4 * (g - ngrp);
+    T y[4][KB];
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int c = 0; c < KB; ++c) y[t][c] = at(k + c, j0 + t);
+#pragma unroll
+    for (int c = 1; c < KB; ++c)
+#pragma unroll
+      for (int p = 0; p < c; ++p) {
+        const T l = at(k + c, k + p);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) y[t][c] -= l * y[t][p];
+      }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int c = 0; c < KB; ++c) at(k + c, j0 + t) = y[t][c];
+  }
+}
+
+template <typename T, int KB>
+__global__ void k_dense_update(DevPlan P, DevState S, int k, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int lane = threadIdx.x;
+  const int tile = blockIdx.y;
+  if (!tile_active(S, tile, lane)) return;
+  const int ld = P.ndp;
+  const int r0 = k + KB;
+  const int nb = (ld - r0) / 4;
+  const int t = blockIdx.x * blockDim.y + threadIdx.y;
+  if (t >= nb * nb) return;
+  const int bi = t % nb, bj = t / nb;
+  const int i0 = r0 + 4 * bi, j0 = r0 + 4 * bj;
+  T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
+  auto at = [&](int r, int c) -> T& { return A[((size_t)c * ld + r) * kTile]; };
+  T acc[4][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) acc[r][c] = at(i0 + r, j0 + c);
+#pragma unroll
+  for (int p = 0; p < KB; ++p) {
+    T a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[r] = at(i0 + r, k + p);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) b[c] = at(k + p, j0 + c);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[r][c] -= a[r] * b[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int r = 0; r < 4; ++r) at(i0 + r, j0 + c) = acc[r][c];
+}
+
+// ---------------------------------------------------------------------------
+// Forward / backward substitution (Sec. 4.3.3).  Row-oriented gathers per
+// level instead of the paper's atomicAdd scatter: every row writes only its
+// own entry, so the result is deterministic.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_fwd_level(DevPlan P, DevState S, int r0, int r1, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int lane = threadIdx.x;
+  const int ri = r0 + blockIdx.x * blockDim.y + threadIdx.y;
+  const int tile = blockIdx.y;
+  if (ri >= r1) return;
+  if (!tile_active(S, tile, lane)) return;
+  const T* __restrict__ LU = reinterpret_cast<const T*>(S.lu) + (size_t)tile * P.NLU * kTile + lane;
+  T* __restrict__ X = reinterpret_cast<T*>(S.x) + (size_t)tile * P.mp * kTile + lane;
+  const int i = P.fw_rows[ri];
+  T acc = X[(size_t)i * kTile];
+  const int e0 = P.fw_ptr[ri], e1 = P.fw_ptr[ri + 1];
+  for (int e = e0; e < e1; ++e) acc -= LU[(size_t)P.fw_pos[e] * kTile] * X[(size_t)P.fw_col[e] * kTile];
+  X[(size_t)i * kTile] = acc;
+}
+
+template <typename T>
+__global__ void k_bwd_level(DevPlan P, DevState S, int r0, int r1, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int lane = threadIdx.x;
+  const int ri = r0 + blockIdx.x * blockDim.y + threadIdx.y;
+  const int tile = blockIdx.y;
+  if (ri >= r1) return;
+  if (!tile_active(S, tile, lane)) return;
+  const T* __restrict__ LU = reinterpret_cast<const T*>(S.lu) + (size_t)tile * P.NLU * kTile + lane;
+  T* __restrict__ X = reinterpret_cast<T*>(S.x) + (size_t)tile * P.mp * kTile + lane;
+  const int i = P.bw_rows[ri];
+  T acc = X[(size_t)i * kTile];
+  const int e0 = P.bw_ptr[ri], e1 = P.bw_ptr[ri + 1];
+  for (int e = e0; e < e1; ++e) acc -= LU[(size_t)P.bw_pos[e] * kTile] * X[(size_t)P.bw_col[e] * kTile];
+  X[(size_t)i * kTile] = acc / LU[(size_t)P.dp[i] * kTile];
+}
+
+// Dense block solves, one lane per instance: unit-lower forward, then upper
+// backward substitution on rows s .. s+ndp-1 of the right-hand side.
+template <typename T>
+__global__ void k_dense_solve(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int lane = threadIdx.x;
+  const int tile = blockIdx.x * blockDim.y + threadIdx.y;
+  if (tile * kTile >= S.Bp) return;
+  if (!tile_active(S, tile, lane)) return;
+  const T* __restrict__ A = reinterpret_cast<const T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
+  T* __restrict__ X = reinterpret_cast<T*>(S.x) + ((size_t)tile * P.mp + P.s) * kTile + lane;
+  const int ld = P.ndp;
+  for (int c = 0; c < ld; ++c) {  // column-oriented forward: x[r] -= L[r][c] x[c]
+    const T xc = X[(size_t)c * kTile];
+    for (int r = c + 1; r < ld; ++r) X[(size_t)r * kTile] -= A[((size_t)c * ld + r) * kTile] * xc;
+  }
+  for (int c = ld - 1; c >= 0; --c) {  // column-oriented backward
+    const T xc = X[(size_t)c * kTile] / A[((size_t)c * ld + c) * kTile];
+    X[(size_t)c * kTile] = xc;
+    for (int r = 0; r < c; ++r) X[(size_t)r * kTile] -= A[((size_t)c * ld + r) * kTile] * xc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Voltage update (Sec. 3, step 4): th[PV+PQ] += dx, |V|[PQ] += dx, then the
+// rectangular form and 1/|V| for the next mismatch.  Inactive instances keep
+// their voltages.  A non-finite step marks the instance failed.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_update(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  const int lane = threadIdx.x;
+  const int tile = blockIdx.y;
+  const int i = blockIdx.x * blockDim.y + threadIdx.y;
+  if (i >= P.n) return;
+  const int b = tile * kTile + lane;
+  if (!S.active[b]) return;
+  const int bt = P.bus_type[i];
+  if (bt == 3) return;
+  const T* __restrict__ X = reinterpret_cast<const T*>(S.x) + (size_t)tile * P.mp * kTile + lane;
+  const size_t o = sidx(tile, P.n, i, lane);
+  const double dth = (double)X[(size_t)P.rhs_p[i] * kTile];
+  double va = S.va[o] + dth;
+  double vm = S.vm[o];
+  bool ok = fabs(dth) <= DBL_MAX;
+  if (bt == 1) {
+    const double dvm = (double)X[(size_t)P.rhs_q[i] * kTile];
+    ok = ok && fabs(dvm) <= DBL_MAX;
+    vm += dvm;
+  }
+  if (!ok) {
+    S.bad[b] = 1;
+    return;
+  }
+  double sn, cs;
+  sincos(va, &sn, &cs);
+  S.va[o] = va;
+  S.vm[o] = vm;
+  S.ve[o] = vm * cs;
+  S.vf[o] = vm * sn;
+  S.vinv[o] = 1.0 / vm;
+}
+
+// Scatter a user right-hand side [B, m] (J row order) into the permuted rhs,
+// and gather the solution back into J column order.
+template <typename T>
+__global__ void k_rhs_in(DevPlan P, DevState S, int B, const double* __restrict__ rhs) {
+  const int lane = threadIdx.x, tile = blockIdx.y;
+  const int u = blockIdx.x * blockDim.y + threadIdx.y;
+  if (u >= P.m) return;
+  const int b = tile * kTile + lane;
+  T* X = reinterpret_cast<T*>(S.x) + (size_t)tile * P.mp * kTile + lane;
+  X[(size_t)P.unk_pos[u] * kTile] = b < B ? (T)rhs[(size_t)b * P.m + u] : (T)0;
+}
+
+template <typename T>
+__global__ void k_rhs_out(DevPlan P, DevState S, int B, double* __restrict__ dx) {
+  const int lane = threadIdx.x, tile = blockIdx.y;
+  const int u = blockIdx.x * blockDim.y + threadIdx.y;
+  if (u >= P.m) return;
+  const int b = tile * kTile + lane;
+  const T* X = reinterpret_cast<const T*>(S.x) + (size_t)tile * P.mp * kTile + lane;
+  if (b < B) dx[(size_t)b * P.m + u] = (double)X[(size_t)P.unk_pos[u] * kTile];
+}
+
+// F in J row order and the norm, for the mismatch stage entry point.
+template <typename T>
+__global__ void k_f_out(DevPlan P, DevState S, int B, double* __restrict__ F, double* __restrict__ norm) {
+  const int lane = threadIdx.x, tile = blockIdx.y;
+  const int u = blockIdx.x * blockDim.y + threadIdx.y;
+  const int b = tile * kTile + lane;
+  if (b >= B) return;
+  if (u < P.m) {
+    const T* X = reinterpret_cast<const T*>(S.x) + (size_t)tile * P.mp * kTile + lane;
+    F[(size_t)b * P.m + u] = -(double)X[(size_t)P.unk_pos[u] * kTile];
+  }
+  if (u == 0) norm[b] = __longlong_as_double((long long)S.norm[b]);
+}
+
+// LU values of the pattern (CCS order of pf_plan_get_pattern) out to [B, nnz].
+template <typename T>
+__global__ void k_lu_out(DevPlan P, DevState S, int B, const int64_t* __restrict__ map, int64_t nnz,
+                         double* __restrict__ out) {
+  const int lane = threadIdx.x, tile = blockIdx.y;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+  if (q >= nnz) return;
+  const int b = tile * kTile + lane;
+  if (b >= B) return;
+  const T* LU = reinterpret_cast<const T*>(S.lu) + (size_t)tile * P.NLU * kTile + lane;
+  out[(size_t)b * nnz + q] = (double)LU[(size_t)map[q] * kTile];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host-side launchers
+// ---------------------------------------------------------------------------
+static inline dim3 grid2(int64_t items, int per_block, int tiles) {
+  return dim3((unsigned)((items + per_block - 1) / per_block), (unsigned)tiles);
+}
+
+void launch_load(const DevPlan& P, const DevState& S, int B, const double* sbus, const double* v0,
+                 cudaStream_t st) {
+  dim3 g((P.n + 31) / 32, S.Bp / kTile);
+  k_load<<<g, dim3(32, 8), 0, st>>>(P, S, B, reinterpret_cast<const double2*>(sbus),
+                                    reinterpret_cast<const double2*>(v0));
+}
+
+void launch_store(const DevPlan& P, const DevState& S, int B, double* v_out, int32_t* iters,
+                  uint8_t* status, cudaStream_t st) {
+  dim3 g((P.n + 31) / 32, S.Bp / kTile);
+  k_store<<<g, dim3(32, 8), 0, st>>>(P, S, B, reinterpret_cast<double2*>(v_out), iters, status);
+}
+
+template <typename T>
+void launch_mismatch(const DevPlan& P, const DevState& S, int jac, const int32_t* gate, cudaStream_t st) {
+  dim3 g((P.n + kMWarps * kBusPerWarp - 1) / (kMWarps * kBusPerWarp), S.Bp / kTile);
+  k_mismatch_jac<T><<<g, dim3(32, kMWarps), 0, st>>>(P, S, jac, gate);
+}
+
+void launch_check(const DevState& S, int it, int maxit, double tol, int32_t* counter, cudaStream_t st) {
+  k_check<<<(S.Bp + 255) / 256, 256, 0, st>>>(S, S.Bp, it, maxit, tol, counter);
+}
+
+template <typename T>
+void launch_prepare_lu(const DevPlan& P, const DevState& S, const int32_t* gate, cudaStream_t st) {
+  const size_t n16 = (size_t)P.NLU * S.Bp * sizeof(T) / 16;  // NLU*Bp*sizeof(T) is a multiple of 128
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_zero16<<<sms * 8, 256, 0, st>>>(reinterpret_cast<uint4*>(S.lu), n16, gate);
+  if (P.n_one > 0) k_set_ones<T><<<dim3(1, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate);
+}
+
+template <typename T>
+void launch_factor(const DevPlan& P, const DevState& S, const std::vector<int32_t>& lvl_ptr,
+                   const int32_t* gate, cudaStream_t st) {
+  const int tiles = S.Bp / kTile;
+  for (size_t l = 0; l + 1 < lvl_ptr.size(); ++l) {
+    int c0 = lvl_ptr[l], c1 = lvl_ptr[l + 1];
+    if (c1 <= c0) continue;
+    k_lu_sparse_level<T><<<grid2(c1 - c0, kLWarps, tiles), dim3(32, kLWarps), 0, st>>>(P, S, c0, c1, gate);
+  }
+  const int ld = P.ndp;
+  for (int k = 0; k < ld; k += P.kb) {
+    const int rem = ld - k - P.kb;
+    switch (P.kb) {
+      case 4:
+        k_dense_diag<T, 4><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, k, gate);
+        if (rem > 0) {
+          k_dense_panel<T, 4><<<grid2(2 * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
+          k_dense_update<T, 4><<<grid2((int64_t)(rem / 4) * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
+        }
+        break;
+      case 8:
+        k_dense_diag<T, 8><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, k, gate);
+        if (rem > 0) {
+          k_dense_panel<T, 8><<<grid2(2 * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
+          k_dense_update<T, 8><<<grid2((int64_t)(rem / 4) * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
+        }
+        break;
+      default:
+        k_dense_diag<T, 16><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, k, gate);
+        if (rem > 0) {
+          k_dense_panel<T, 16><<<grid2(2 * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
+          k_dense_update<T, 16><<<grid2((int64_t)(rem / 4) * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
+        }
+        break;
+    }
+  }
+}
+
+template <typename T>
+void launch_solve(const DevPlan& P, const DevState& S, const std::vector<int32_t>& fw_lvl,
+                  const std::vector<int32_t>& bw_lvl, const int32_t* gate, cudaStream_t st) {
+  const int tiles = S.Bp / kTile;
+  for (size_t l = 0; l + 1 < fw_lvl.size(); ++l) {
+    int r0 = fw_lvl[l], r1 = fw_lvl[l + 1];
+    if (r1 > r0) k_fwd_level<T><<<grid2(r1 - r0, 4, tiles), dim3(32, 4), 0, st>>>(P, S, r0, r1, gate);
+  }
+  if (P.ndp > 0) k_dense_solve<T><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, gate);
+  for (size_t l = 0; l + 1 < bw_lvl.size(); ++l) {
+    int r0 = bw_lvl[l], r1 = bw_lvl[l + 1];
+    if (r1 > r0) k_bwd_level<T><<<grid2(r1 - r0, 4, tiles), dim3(32, 4), 0, st>>>(P, S, r0, r1, gate);
+  }
+}
+
+template <typename T>
+void launch_update(const DevPlan& P, const DevState& S, const int32_t* gate, cudaStream_t st) {
+  k_update<T><<<grid2(P.n, 8, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate);
+}
+
+template <typename T>
+void launch_rhs_in(const DevPlan& P, const DevState& S, int B, const double* rhs, cudaStream_t st) {
+  cudaMemsetAsync(S.x, 0, (size_t)P.mp * S.Bp * sizeof(T), st);
+  if (P.m > 0) k_rhs_in<T><<<grid2(P.m, 8, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, B, rhs);
+}
+
+template <typename T>
+void launch_rhs_out(const DevPlan& P, const DevState& S, int B, double* dx, cudaStream_t st) {
+  if (P.m > 0) k_rhs_out<T><<<grid2(P.m, 8, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, B, dx);
+}
+
+template <typename T>
+void launch_f_out(const DevPlan& P, const DevState& S, int B, double* F, double* norm, cudaStream_t st) {
+  k_f_out<T><<<grid2(P.m > 0 ? P.m : 1, 8, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, B, F, norm);
+}
+
+template <typename T>
+void launch_lu_out(const DevPlan& P, const DevState& S, int B, const int64_t* map, int64_t nnz, double* out,
+                   cudaStream_t st) {
+  if (nnz > 0) k_lu_out<T><<<grid2(nnz, 8, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, B, map, nnz, out);
+}
+
+#define NRPF_INST(T)                                                                                        \
+  template void launch_mismatch<T>(const DevPlan&, const DevState&, int, const int32_t*, cudaStream_t);    \
+  template void launch_prepare_lu<T>(const DevPlan&, const DevState&, const int32_t*, cudaStream_t);       \
+  template void launch_factor<T>(const DevPlan&, const DevState&, const std::vector<int32_t>&,             \
+                                 const int32_t*, cudaStream_t);                                            \
+  template void launch_solve<T>(const DevPlan&, const DevState&, const std::vector<int32_t>&,              \
+                                const std::vector<int32_t>&, const int32_t*, cudaStream_t);                \
+  template void launch_update<T>(const DevPlan&, const DevState&, const int32_t*, cudaStream_t);           \
+  template void launch_rhs_in<T>(const DevPlan&, const DevState&, int, const double*, cudaStream_t);       \
+  template void launch_rhs_out<T>(const DevPlan&, const DevState&, int, double*, cudaStream_t);            \
+  template void launch_f_out<T>(const DevPlan&, const DevState&, int, double*, double*, cudaStream_t);     \
+  template void launch_lu_out<T>(const DevPlan&, const DevState&, int, const int64_t*, int64_t, double*,   \
+                                 cudaStream_t);
+
+NRPF_INST(double)
+NRPF_INST(float)
+
+}  // namespace nrpf

@@ -1,0 +1,149 @@
+"""Python face of the batched Newton-Raphson library: a plan object whose
+methods pass torch CUDA tensors (device memory, the caller's stream) to the C
+ABI.  No arithmetic of the method happens here."""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+_PREC = {"fp64": _lib.LU_FP64, "fp32": _lib.LU_FP32}
+_ORDER = {"amd": _lib.ORDER_AMD, "natural": _lib.ORDER_NATURAL}
+
+
+def _dptr(t: torch.Tensor) -> C.c_void_p:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream() -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Plan:
+    """Symbolic plan for one Ybus sparsity pattern (pf_plan_create)."""
+
+    def __init__(self, n, rowptr, colidx, y_re, y_im, bus_type, lu_precision="fp64",
+                 ordering="amd", dense_frac=0.7, panel=8, max_batch=0, host_only=False):
+        self.n = int(n)
+        self._rowptr = np.ascontiguousarray(rowptr, np.int32)
+        self._colidx = np.ascontiguousarray(colidx, np.int32)
+        self._yre = np.ascontiguousarray(y_re, np.float64)
+        self._yim = np.ascontiguousarray(y_im, np.float64)
+        self._bt = np.ascontiguousarray(bus_type, np.int8)
+        opt = _lib.pf_options()
+        lib.pf_options_default(C.byref(opt))
+        opt.lu_precision = _PREC[lu_precision]
+        opt.ordering = _ORDER[ordering]
+        opt.dense_frac = float(dense_frac)
+        opt.panel = int(panel)
+        opt.max_batch = int(max_batch)
+        opt.host_only = int(bool(host_only))
+        h = C.c_void_p()
+        check(lib.pf_plan_create(self.n, _lib._np_ptr(self._rowptr), _lib._np_ptr(self._colidx),
+                                 _lib._np_ptr(self._yre), _lib._np_ptr(self._yim), _lib._np_ptr(self._bt),
+                                 C.byref(opt), C.byref(h)), "pf_plan_create")
+        self._h = h
+        self.lu_precision = lu_precision
+
+    @classmethod
+    def from_branches(cls, n, f, t, r, x, b, bus_type, **kw):
+        rowptr, colidx, yre, yim = _lib.ybus_from_branches(n, f, t, r, x, b)
+        return cls(n, rowptr, colidx, yre, yim, bus_type, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.pf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def info(self) -> dict:
+        inf = _lib.pf_plan_info()
+        check(lib.pf_plan_get_info(self._h, C.byref(inf)), "pf_plan_get_info")
+        return {k: getattr(inf, k) for k, _ in _lib.pf_plan_info._fields_}
+
+    def pattern(self):
+        """(pos_of_unknown [m], colptr [m+1], rowidx [nnz]) of A = P J P^T."""
+        m = self.info["m"]
+        nnz = C.c_int64(0)
+        check(lib.pf_plan_get_pattern(self._h, None, None, None, C.byref(nnz)), "pattern")
+        pos = np.zeros(m, np.int32)
+        colptr = np.zeros(m + 1, np.int64)
+        rowidx = np.zeros(max(nnz.value, 1), np.int32)
+        check(lib.pf_plan_get_pattern(self._h, _lib._np_ptr(pos), _lib._np_ptr(colptr),
+                                      _lib._np_ptr(rowidx), C.byref(nnz)), "pattern")
+        return pos, colptr, rowidx[:nnz.value]
+
+    # ---- solves (device tensors, caller's current stream) ----
+    def solve(self, sbus: torch.Tensor, v0: torch.Tensor, tol: float = 1e-8, maxit: int = 10,
+              out=None):
+        """Newton-Raphson for a batch: sbus, v0 complex128 [B, n] on the GPU.
+        Returns (v [B, n] complex128, iters [B] int32, status [B] uint8)."""
+        B = sbus.shape[0]
+        self._check_bn(sbus, B)
+        self._check_bn(v0, B)
+        dev = sbus.device
+        if out is None:
+            v = torch.empty((B, self.n), dtype=torch.complex128, device=dev)
+            iters = torch.empty(B, dtype=torch.int32, device=dev)
+            status = torch.empty(B, dtype=torch.uint8, device=dev)
+        else:
+            v, iters, status = out
+        check(lib.pf_solve_batch(self._h, B, _dptr(sbus), _dptr(v0), float(tol), int(maxit), _dptr(v),
+                                 _dptr(iters), _dptr(status), _stream()), "pf_solve_batch")
+        return v, iters, status
+
+    def stage_mismatch(self, sbus, v):
+        B = v.shape[0]
+        self._check_bn(sbus, B)
+        self._check_bn(v, B)
+        m = self.info["m"]
+        F = torch.empty((B, m), dtype=torch.float64, device=v.device)
+        norm = torch.empty(B, dtype=torch.float64, device=v.device)
+        check(lib.pf_stage_mismatch(self._h, B, _dptr(sbus), _dptr(v), _dptr(F), _dptr(norm), _stream()),
+              "pf_stage_mismatch")
+        return F, norm
+
+    def stage_factor(self, v, factor=True):
+        B = v.shape[0]
+        self._check_bn(v, B)
+        nnz = C.c_int64(0)
+        check(lib.pf_plan_get_pattern(self._h, None, None, None, C.byref(nnz)), "pattern")
+        lu = torch.empty((B, nnz.value), dtype=torch.float64, device=v.device)
+        check(lib.pf_stage_factor(self._h, B, _dptr(v), int(bool(factor)), _dptr(lu), _stream()),
+              "pf_stage_factor")
+        return lu
+
+    def stage_linear_solve(self, v, rhs):
+        B = v.shape[0]
+        self._check_bn(v, B)
+        m = self.info["m"]
+        if rhs.shape != (B, m) or rhs.dtype != torch.float64:
+            raise ValueError("rhs must be float64 [B, m]")
+        dx = torch.empty((B, m), dtype=torch.float64, device=v.device)
+        check(lib.pf_stage_linear_solve(self._h, B, _dptr(v), _dptr(rhs), _dptr(dx), _stream()),
+              "pf_stage_linear_solve")
+        return dx
+
+    def _check_bn(self, t, B):
+        if t.dtype != torch.complex128 or t.shape != (B, self.n):
+            raise ValueError(f"expected complex128 [{B}, {self.n}], got {t.dtype} {tuple(t.shape)}")

@@ -1,0 +1,218 @@
+"""GPU parity: every stage and the whole solve, through the C ABI, against the
+CPU FP64 oracle on the same seeded inputs.
+
+Tolerances (float64 everywhere on the FP64 path):
+  * mismatch F, Jacobian entries: 1e-10 absolute (sums of a handful of O(10)
+    products; only the summation order differs);
+  * factorisation: ||L U - P J P^T||_max <= 1e-10 ||J||_max;
+  * linear solve: ||dx - dx_oracle||_max <= 1e-8 (1 + ||dx_oracle||_max);
+  * Newton result: equal status and iteration counts, |d|V|| <= 1e-6 p.u.,
+    |d theta| <= 1e-6 rad, and the oracle's mismatch at the GPU's voltages
+    below the tolerance 1e-8 p.u.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+torch = pytest.importorskip("torch")
+
+from oracle import nrpf  # noqa: E402
+from tests.common import case, oracle_ybus, perturbed, permuted_dense  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+def _pf():
+    import paper_2101_02270_gb300 as pf
+    return pf
+
+
+def _plan(g, **kw):
+    return _pf().Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, **kw)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _oracle_solve(g, S, V0, tol=TOL, maxit=10, idx=None):
+    Y = oracle_ybus(g)
+    idx = range(S.shape[0]) if idx is None else idx
+    out = [nrpf.newton(Y, S[b], V0[b], g.bus_type, tol, maxit) for b in idx]
+    return (np.array([o[0] for o in out]), np.array([o[1] for o in out]), np.array([o[2] for o in out]))
+
+
+def _compare_newton(g, Vg, itg, stg, Vo, ito, sto, S, check_iters=True):
+    assert np.array_equal(stg, sto)
+    if check_iters:
+        assert np.array_equal(itg, ito)
+    ok = sto == 0
+    dvm = np.abs(np.abs(Vg[ok]) - np.abs(Vo[ok]))
+    dth = np.abs(np.angle(Vg[ok] * np.conj(Vo[ok])))
+    assert dvm.max(initial=0) <= 1e-6 and dth.max(initial=0) <= 1e-6
+    Y = oracle_ybus(g)
+    _, pv, pq, _ = nrpf.bus_sets(g.bus_type)
+    for b in np.flatnonzero(ok):
+        F = nrpf.mismatch(Y, Vg[b], S[b], pv, pq)
+        assert np.max(np.abs(F)) < TOL
+
+
+@pytest.mark.parametrize("name,B", [("mesh30_b64", 64), ("mesh30_b64", 37), ("mesh2000_b10k", 45)])
+def test_mismatch_stage(name, B):
+    g, S, V0 = case(name, batch=B)
+    V = perturbed(V0, seed=3)
+    with _plan(g) as p:
+        F, norm = p.stage_mismatch(_dev(S), _dev(V))
+        F = F.cpu().numpy()
+        norm = norm.cpu().numpy()
+    Y = oracle_ybus(g)
+    _, pv, pq, _ = nrpf.bus_sets(g.bus_type)
+    for b in range(B):
+        Fo = nrpf.mismatch(Y, V[b], S[b], pv, pq)
+        assert np.max(np.abs(F[b] - Fo)) < 1e-10
+        assert abs(norm[b] - np.max(np.abs(Fo))) < 1e-10
+
+
+@pytest.mark.parametrize("name,B,kw", [("mesh30_b64", 40, {}), ("mesh30_b64", 33, {"ordering": "natural"}),
+                                       ("mesh2000_b10k", 3, {})])
+def test_jacobian_and_factor_stage(name, B, kw):
+    g, S, V0 = case(name, batch=B)
+    V = perturbed(V0, seed=4)
+    with _plan(g, **kw) as p:
+        pos, colptr, rowidx = p.pattern()
+        A = p.stage_factor(_dev(V), factor=False).cpu().numpy()
+        LU = p.stage_factor(_dev(V), factor=True).cpu().numpy()
+        m = p.info["m"]
+    Y = oracle_ybus(g)
+    _, pv, pq, _ = nrpf.bus_sets(g.bus_type)
+    inv = np.empty(m, int)
+    inv[pos] = np.arange(m)
+    for b in range(B):
+        J = nrpf.jacobian(Y, V[b], pv, pq).toarray()
+        PJP = J[np.ix_(inv, inv)]  # row/col r of A is J row/col inv[r]
+        Ag = permuted_dense(colptr, rowidx, A[b], m)
+        assert np.max(np.abs(Ag - PJP)) < 1e-10
+        F = permuted_dense(colptr, rowidx, LU[b], m)
+        L = np.tril(F, -1) + np.eye(m)
+        U = np.triu(F)
+        assert np.max(np.abs(L @ U - PJP)) <= 1e-10 * np.max(np.abs(J))
+
+
+@pytest.mark.parametrize("name,B,kw", [("mesh30_b64", 64, {}), ("mesh30_b64", 70, {"panel": 4}),
+                                       ("mesh30_b64", 32, {"panel": 16}), ("mesh2000_b10k", 8, {})])
+def test_linear_solve_stage(name, B, kw):
+    g, S, V0 = case(name, batch=B)
+    V = perturbed(V0, seed=5)
+    rng = np.random.default_rng(9)
+    with _plan(g, **kw) as p:
+        m = p.info["m"]
+        rhs = rng.standard_normal((B, m))
+        dx = p.stage_linear_solve(_dev(V), _dev(rhs)).cpu().numpy()
+    Y = oracle_ybus(g)
+    _, pv, pq, _ = nrpf.bus_sets(g.bus_type)
+    for b in range(B):
+        J = nrpf.jacobian(Y, V[b], pv, pq)
+        xo = spla.spsolve(J.tocsc(), rhs[b])
+        assert np.max(np.abs(dx[b] - xo)) <= 1e-8 * (1 + np.max(np.abs(xo)))
+
+
+@pytest.mark.parametrize("B", [64, 1, 45])
+def test_newton_mesh30(B):
+    g, S, V0 = case("mesh30_b64", batch=B)
+    with _plan(g) as p:
+        v, it, st = p.solve(_dev(S), _dev(V0), TOL, 10)
+        Vg, itg, stg = v.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+    Vo, ito, sto = _oracle_solve(g, S, V0)
+    _compare_newton(g, Vg, itg, stg, Vo, ito, sto, S)
+
+
+def test_newton_mesh2000_ragged():
+    g, S, V0 = case("mesh2000_b10k", batch=70)
+    with _plan(g) as p:
+        v, it, st = p.solve(_dev(S), _dev(V0), TOL, 10)
+        Vg, itg, stg = v.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+    idx = list(range(0, 70, 3))
+    Vo, ito, sto = _oracle_solve(g, S, V0, idx=idx)
+    _compare_newton(g, Vg[idx], itg[idx], stg[idx], Vo, ito, sto, S[idx])
+
+
+def test_newton_mesh2000_full_batch_sampled():
+    """The benchmark's launch configuration (10,000 scenarios); outputs sampled."""
+    g, S, V0 = case("mesh2000_b10k")
+    with _plan(g) as p:
+        v, it, st = p.solve(_dev(S), _dev(V0), TOL, 10)
+        Vg, itg, stg = v.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+    idx = list(np.random.default_rng(0).choice(S.shape[0], 24, replace=False)) + [0, S.shape[0] - 1]
+    Vo, ito, sto = _oracle_solve(g, S, V0, idx=idx)
+    _compare_newton(g, Vg[idx], itg[idx], stg[idx], Vo, ito, sto, S[idx])
+    # properties at any size: every instance converged, the recomputed
+    # mismatch of a further sample is below tolerance
+    assert np.all(stg == 0)
+
+
+def test_edge_cases():
+    pf = _pf()
+    g, S, V0 = case("mesh30_b64", batch=8)
+    Vo, ito, sto = _oracle_solve(g, S, V0, tol=1e-12, maxit=20)
+    with _plan(g) as p:
+        # B == 0 is a no-op
+        assert pf.lib.pf_solve_batch(p._h, 0, None, None, 1e-8, 10, None, None, None, None) == 0
+        # maxit = 0
+        v, it, st = p.solve(_dev(S), _dev(V0), TOL, 0)
+        assert np.all(it.cpu().numpy() == 0) and np.all(st.cpu().numpy() == 1)
+        # starting at the solution: zero updates
+        v, it, st = p.solve(_dev(S), _dev(Vo), TOL, 10)
+        assert np.all(it.cpu().numpy() == 0) and np.all(st.cpu().numpy() == 0)
+        # tol = 0 cannot be met: maxit updates
+        v, it, st = p.solve(_dev(S), _dev(V0), 0.0, 6)
+        assert np.all(it.cpu().numpy() == 6) and np.all(st.cpu().numpy() == 1)
+        # a non-finite injection fails that instance only
+        Sb = S.copy()
+        Sb[3, 5] = np.nan
+        v, it, st = p.solve(_dev(Sb), _dev(V0), TOL, 10)
+        st = st.cpu().numpy()
+        it = it.cpu().numpy()
+        assert st[3] == 2 and it[3] == 0
+        assert np.all(np.delete(st, 3) == 0)
+        # bad arguments
+        assert pf.lib.pf_solve_batch(p._h, -1, None, None, 1e-8, 10, None, None, None, None) == -1
+        assert pf.lib.pf_solve_batch(p._h, 1, None, None, float("nan"), 10, None, None, None, None) == -1
+
+
+def test_singular_instance_reports_failure():
+    """An instance whose Jacobian is singular (a PQ bus with zero voltage)
+    stops with status 2 while the rest of the batch converges."""
+    g, S, V0 = case("mesh30_b64", batch=4)
+    V0 = V0.copy()
+    V0[1, 7] = 0.0
+    with _plan(g) as p:
+        v, it, st = p.solve(_dev(S), _dev(V0), TOL, 10)
+        st = st.cpu().numpy()
+    assert st[1] == 2 and np.all(st[[0, 2, 3]] == 0)
+
+
+def test_plan_reuse_and_capacity_growth():
+    g, S, V0 = case("mesh30_b64", batch=64)
+    with _plan(g, max_batch=16) as p:
+        a = p.solve(_dev(S[:16]), _dev(V0[:16]), TOL, 10)
+        b = p.solve(_dev(S), _dev(V0), TOL, 10)  # grows the workspace
+        c = p.solve(_dev(S[:16]), _dev(V0[:16]), TOL, 10)
+        assert torch.equal(a[0], c[0]) and torch.equal(a[1], c[1])
+        assert torch.equal(b[0][:16], a[0])
+        assert p.info["capacity"] >= 64
+
+
+@pytest.mark.parametrize("name,B", [("mesh30_b64", 64), ("mesh2000_b10k", 40)])
+def test_mixed_precision_lu(name, B):
+    """FP32 LU + FS/BS, FP64 mismatch/update: same statuses, same tolerance,
+    a few more iterations at most."""
+    g, S, V0 = case(name, batch=B)
+    with _plan(g, lu_precision="fp32") as p:
+        v, it, st = p.solve(_dev(S), _dev(V0), TOL, 20)
+        Vg, itg, stg = v.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
+    idx = list(range(0, B, max(1, B // 10)))
+    Vo, ito, sto = _oracle_solve(g, S, V0, idx=idx)
+    _compare_newton(g, Vg[idx], itg[idx], stg[idx], Vo, ito, sto, S[idx], check_iters=False)
+    assert np.all(itg[idx] >= ito) and np.all(itg[idx] <= ito + 3)

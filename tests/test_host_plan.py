@@ -1,0 +1,160 @@
+"""Host-side logic of the library, no GPU needed: the shared library loads and
+exports every symbol of include/nrpf.h, the Ybus builder agrees with the
+oracle's, and the symbolic plan (ordering, fill pattern, permutation) is
+consistent.  Plans are created with host_only=1 (no device memory)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import gridgen
+from oracle import nrpf
+from tests.common import oracle_ybus
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    import paper_2101_02270_gb300 as pf
+    return pf
+
+
+def test_library_exports_every_declared_symbol():
+    pf = _lib()
+    hdr = open(os.path.join(ROOT, "include", "nrpf.h")).read()
+    declared = set(re.findall(r"\b(pf_\w+)\s*\(", hdr))
+    assert {"pf_plan_create", "pf_solve_batch", "pf_plan_destroy", "pf_status_str"} <= declared
+    raw = C.CDLL(pf._lib.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(raw, name), name
+    assert pf.lib.pf_status_str(0) == b"ok"
+    assert pf.lib.pf_status_str(-2).startswith(b"invalid Ybus")
+
+
+@pytest.mark.parametrize("name", ["mesh30_b64", "mesh2000_b10k"])
+def test_ybus_builder_matches_oracle(name):
+    pf = _lib()
+    g = gridgen.make_grid(name)
+    rowptr, colidx, yre, yim = pf.ybus_from_branches(g.n, g.f, g.t, g.r, g.x, g.b)
+    Y = oracle_ybus(g)
+    assert np.array_equal(rowptr, Y.indptr) and np.array_equal(colidx, Y.indices)
+    assert np.max(np.abs(yre + 1j * yim - Y.data)) < 1e-12
+
+
+def _plan(g, **kw):
+    pf = _lib()
+    return pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, host_only=True, **kw)
+
+
+def _check_pattern(g, plan):
+    info = plan.info
+    m = info["m"]
+    _, pv, pq, pvpq = nrpf.bus_sets(g.bus_type)
+    assert m == pv.size + 2 * pq.size
+    pos, colptr, rowidx = plan.pattern()
+    assert sorted(pos.tolist()) == list(range(m))  # a permutation
+    cols = [set(rowidx[colptr[j]:colptr[j + 1]].tolist()) for j in range(m)]
+    for j in range(m):
+        r = rowidx[colptr[j]:colptr[j + 1]]
+        assert np.all(np.diff(r) > 0) and j in cols[j]
+    # J's pattern (from the oracle's Jacobian at flat start) maps into the LU pattern
+    Y = oracle_ybus(g)
+    V = np.ones(g.n, complex)
+    J = nrpf.jacobian(Y, V, pv, pq).tocoo()
+    for u, w in zip(J.row, J.col):
+        assert pos[u] in cols[pos[w]]
+    # closed under elimination: L(i,k) != 0 and U(k,j) != 0 imply (i,j) stored
+    rows_of = [set() for _ in range(m)]  # U row k -> columns j > k
+    for j in range(m):
+        for k in cols[j]:
+            if k < j:
+                rows_of[k].add(j)
+    for k in range(m):
+        Lk = [i for i in cols[k] if i > k]
+        for j in rows_of[k]:
+            for i in Lk:
+                assert i in cols[j], (i, j, k)
+    return info
+
+
+def test_plan_pattern_mesh30_amd_and_natural():
+    g = gridgen.make_grid("mesh30_b64")
+    a = _check_pattern(g, _plan(g))
+    n = _check_pattern(g, _plan(g, ordering="natural"))
+    d = _check_pattern(g, _plan(g, dense_frac=1.0))
+    assert d["dense_dim"] == 0 and n["dense_dim"] == 0
+    assert a["dense_dim"] > 0 and a["sparse_cols"] + a["dense_dim"] == a["m"]
+    for kb in (4, 8, 16):
+        i = _plan(g, panel=kb).info
+        assert i["dense_pad"] % kb == 0 and i["dense_pad"] >= i["dense_dim"]
+
+
+def test_plan_tree_has_no_fill():
+    """On a radial feeder minimum degree eliminates leaves first: L+U adds no
+    entry to J's pattern (apart from the last dense remainder)."""
+    for g in gridgen.make_feeders(count=3):
+        info = _check_pattern(g, _plan(g, dense_frac=1.0))
+        pos, colptr, rowidx = _plan(g, dense_frac=1.0).pattern()
+        assert colptr[-1] == info["nnz_j"]
+
+
+def test_plan_sizes_mesh2000():
+    g = gridgen.make_grid("mesh2000_b10k")
+    info = _plan(g).info
+    assert info["m"] == 3798 and info["n_slack"] == 1
+    assert info["nnz_j"] == 26016
+    assert 0 < info["dense_dim"] < 600
+    # the dense block carries most of the refactorisation work
+    assert info["dense_pad"] ** 3 / 3 > 0.7 * info["lu_fma"]
+
+
+def test_plan_rejects_bad_inputs():
+    pf = _lib()
+    g = gridgen.make_grid("mesh30_b64")
+    rowptr, colidx, yre, yim = pf.ybus_from_branches(g.n, g.f, g.t, g.r, g.x, g.b)
+    bt = g.bus_type.copy()
+    with pytest.raises(pf.NrpfError, match="Ybus pattern"):
+        bt0 = bt.copy(); bt0[0] = 1
+        pf.Plan(g.n, rowptr, colidx, yre, yim, bt0, host_only=True)  # no slack
+    with pytest.raises(pf.NrpfError, match="Ybus pattern"):
+        bt1 = bt.copy(); bt1[3] = 7
+        pf.Plan(g.n, rowptr, colidx, yre, yim, bt1, host_only=True)
+    # asymmetric pattern: drop one off-diagonal entry of row 0
+    A = sp.csr_matrix((yre + 1j * yim, colidx, rowptr), shape=(g.n, g.n)).tolil()
+    A[0, 1] = 0
+    A = A.tocsr(); A.eliminate_zeros(); A.sort_indices()
+    with pytest.raises(pf.NrpfError, match="Ybus pattern"):
+        pf.Plan(g.n, A.indptr, A.indices, A.data.real, A.data.imag, bt, host_only=True)
+    # missing diagonal
+    A = sp.csr_matrix((yre + 1j * yim, colidx, rowptr), shape=(g.n, g.n)).tolil()
+    A[2, 2] = 0
+    A = A.tocsr(); A.eliminate_zeros(); A.sort_indices()
+    with pytest.raises(pf.NrpfError, match="Ybus pattern"):
+        pf.Plan(g.n, A.indptr, A.indices, A.data.real, A.data.imag, bt, host_only=True)
+    with pytest.raises(pf.NrpfError, match="invalid argument"):
+        pf.Plan(g.n, rowptr, colidx, yre, yim, bt, host_only=True, panel=6)
+    yre2 = yre.copy(); yre2[0] = np.nan
+    with pytest.raises(pf.NrpfError, match="invalid argument"):
+        pf.Plan(g.n, rowptr, colidx, yre2, yim, bt, host_only=True)
+
+
+def test_host_only_plan_refuses_device_work():
+    pf = _lib()
+    g = gridgen.make_grid("mesh30_b64")
+    p = _plan(g)
+    rc = pf.lib.pf_solve_batch(p._h, 1, None, None, 1e-8, 10, None, None, None, None)
+    assert rc == -1
+    rc = pf.lib.pf_stage_mismatch(p._h, 1, None, None, None, None, None)
+    assert rc == -1
+    p.close()
+
+
+def test_ybus_builder_rejects_bad_branches():
+    pf = _lib()
+    with pytest.raises(pf.NrpfError):
+        pf.ybus_from_branches(3, [0], [5], [0.1], [0.1], [0.0])  # bus out of range
+    with pytest.raises(pf.NrpfError):
+        pf.ybus_from_branches(3, [0], [1], [0.0], [0.0], [0.0])  # zero impedance
