@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark: Newton-Raphson AC power flows per second on one GB300.
+
+A step is one pf_solve_batch over the whole batch of the workload (every NR
+iteration: mismatch + Jacobian refill, sparse + dense LU refactor, FS/BS,
+update, until max|F| < 1e-8 p.u. or maxit) with inputs resident in HBM.
+Default workload: 2,000-bus meshed synthetic grid, 10,000 load scenarios,
+plain FP64, flat start, tol 1e-8, maxit 10 (``--config`` / ``--lu`` select
+other workloads).  Prints one JSON line.
+
+Multi-GPU (torchrun): every rank solves its own batch (weak scaling, no data
+exchange); barrier + max-over-ranks timing.
+``--impl reference`` times the CPU FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gridgen  # noqa: E402
+
+METRIC = "NR power flows/sec at 1e-8 p.u. mismatch on 1 GB300; % of HBM roofline"
+UNIT = "flows/s"
+TOL = 1e-8
+MAXIT = 10
+# Peaks: HBM copy bandwidth from the pool's measurement file; FP64 / FP32 FMA
+# throughput measured live by pf_fma_peak (independent FMA chains on every SM).
+HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes (read + write) of one k_dense_update launch per instance and per
+# trailing-matrix entry r^2, from the ncu capture summarised in
+# profiles/dense_update_fp64_mesh2000.md (batch 640, panel 8, r = 200).
+DENSE_UPDATE_DRAM_B_PER_R2 = 14.3
+
+
+def measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="mesh2000_b10k", choices=list(gridgen.CONFIGS))
+    ap.add_argument("--batch", type=int, default=0, help="override the batch size (0 = the workload's)")
+    ap.add_argument("--lu", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--maxit", type=int, default=MAXIT)
+    ap.add_argument("--dense-frac", type=float, default=0.7)
+    ap.add_argument("--panel", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(g, S, V0, seconds, cores):
+    """Time the CPU oracle on a bounded sample of the workload: a first
+    calibration run sizes the sample to about `seconds` of work on `cores`
+    processes."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import nrpf
+    Y = nrpf.make_ybus(g.n, g.f, g.t, g.r, g.x, g.b)
+    t0 = time.perf_counter()
+    nrpf.newton_batch(Y, S[:1], V0[:1], g.bus_type, TOL, MAXIT)
+    t1 = max(time.perf_counter() - t0, 1e-4)
+    size = int(max(cores, min(S.shape[0], seconds * cores / t1)))
+    size = min(size, S.shape[0])
+    t0 = time.perf_counter()
+    _, it, st = nrpf.newton_batch(Y, S[:size], V0[:size], g.bus_type, TOL, MAXIT, workers=cores)
+    dt = time.perf_counter() - t0
+    conv = int(np.sum(st == 0))
+    return {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {size} of {S.shape[0]} scenarios, scipy SuperLU per Newton step, "
+                      f"{cores} spawn processes, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    name = args.config
+    g = gridgen.make_grid(name)
+    sc = gridgen.config_scenarios(name, g, batch=args.batch or None)
+    S, V0 = sc.sbus(g), sc.v0_flat(g)
+    cores = os.cpu_count() or 1
+    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        oracle_sample(g, S, V0, min(per_step, 2.0), cores)
+    vals = []
+    last = None
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        last = oracle_sample(g, S, V0, per_step, cores)
+        vals.append(last["value"])
+    dt = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": name, "batch": int(S.shape[0]), "tol": TOL,
+                                            "maxit": MAXIT},
+            "cpu_baseline": dict(last, value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def dense_update_flop(ndp, kb):
+    """Algorithmic flops of the trailing updates of one dense refactor:
+    sum over panels k of 2 * r_k^2 * kb, r_k = ndp - k - kb."""
+    tot = 0
+    for k in range(0, ndp, kb):
+        r = ndp - k - kb
+        if r > 0:
+            tot += 2 * r * r * kb
+    return tot
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import ctypes as C
+
+    import paper_2101_02270_gb300 as pf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    name = args.config
+    g = gridgen.make_grid(name)
+    sc = gridgen.config_scenarios(name, g, batch=args.batch or None, seed=1 + rank)
+    S_np, V0_np = sc.sbus(g), sc.v0_flat(g)
+    B = S_np.shape[0]
+    S = torch.from_numpy(S_np).to(dev)
+    V0 = torch.from_numpy(V0_np).to(dev)
+    t0 = time.perf_counter()
+    plan = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision=args.lu,
+                                 dense_frac=args.dense_frac, panel=args.panel, max_batch=B)
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    info = plan.info
+    fp64_peak, fp32_peak = pf._lib.fma_peak(C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    out = (torch.empty((B, g.n), dtype=torch.complex128, device=dev),
+           torch.empty(B, dtype=torch.int32, device=dev), torch.empty(B, dtype=torch.uint8, device=dev))
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return plan.solve(S, V0, TOL, args.maxit, out=out)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    plan.profile_start(["dense_update"])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = plan.profile_read()
+    clk = clocks.stop()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    iters = out[1].cpu().numpy()
+    status = out[2].cpu().numpy()
+    conv = int(np.sum(status == 0))
+    conv_t = torch.tensor([conv], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(conv_t)
+    value = float(conv_t.item()) * args.steps / (ms_max / 1e3)
+    launches = int(sum(v[0] for v in prof.values()))
+
+    # ---- end to end through the public API with host buffers ----
+    S_h = torch.from_numpy(S_np).pin_memory()
+    V0_h = torch.from_numpy(V0_np).pin_memory()
+    V_h = torch.empty((B, g.n), dtype=torch.complex128).pin_memory()
+    it_h = torch.empty(B, dtype=torch.int32).pin_memory()
+    st_h = torch.empty(B, dtype=torch.uint8).pin_memory()
+    Sd = torch.empty_like(S)
+    Vd = torch.empty_like(V0)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        Sd.copy_(S_h, non_blocking=True)
+        Vd.copy_(V0_h, non_blocking=True)
+        v, it, st = plan.solve(Sd, Vd, TOL, args.maxit, out=out)
+        V_h.copy_(v, non_blocking=True)
+        it_h.copy_(it, non_blocking=True)
+        st_h.copy_(st, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    ms_e2e = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_e2e, op=dist.ReduceOp.MAX)
+    conv_e2e = int(np.sum(st_h.numpy() == 0)) * world
+    e2e_value = conv_e2e * args.steps / (float(ms_e2e.item()) / 1e3)
+    h2d = 2 * B * g.n * 16
+    d2h = B * g.n * 16 + B * 4 + B
+
+    # ---- roofline of the dominant kernel (dense trailing update) ----
+    w = 8 if args.lu == "fp64" else 4
+    ndp = info["dense_pad"]
+    refactors = int(iters.sum()) * args.steps  # one refactor per Newton update per instance
+    du = prof["dense_update"]
+    du_flop = dense_update_flop(ndp, args.panel) * refactors
+    achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
+    peak = fp64_peak if args.lu == "fp64" else fp32_peak
+    r2 = [(ndp - k - args.panel) ** 2 for k in range(0, ndp, args.panel) if ndp - k - args.panel > 0]
+    traffic = (DENSE_UPDATE_DRAM_B_PER_R2 * B * sum(r2) / len(r2)
+               if r2 and args.lu == "fp64" and args.panel == 8 else None)
+    hbm, hbm_kind = measured_hbm()
+    # whole-step HBM roofline (metric's second half): algorithmic bytes per
+    # instance-iteration = LU written once and read once + voltages, injections,
+    # rhs and solution
+    nnz_lu = info["nnz_lu"]
+    bmin = 2 * w * nnz_lu + 8 * (8 * g.n + 4 * info["m"])
+    step_bytes = bmin * int(iters.sum())
+    hbm_pct = 100.0 * (step_bytes * args.steps / (ms_max / 1e3) / 1e9) / hbm
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.lu == "fp64" else "f64+f32lu",
+        "data": "synthetic",
+        "config": {"workload": name, "batch_per_gpu": B, "buses": g.n, "branches": g.n_branch,
+                   "unknowns": info["m"], "lu_precision": args.lu, "tol": TOL, "maxit": args.maxit,
+                   "load_scale": g.load_scale, "dense_block": info["dense_dim"], "panel": args.panel,
+                   "parallelism": f"instances split over {world} GPU(s)",
+                   "l2": f"working set > L2: LU workspace {nnz_lu * w * B / 1e9:.1f} GB per GPU",
+                   "plan_ms": round(plan_ms, 1)},
+        "iterations": {"mean": float(iters.mean()), "max": int(iters.max()),
+                       "hist": np.bincount(iters).tolist()},
+        "converged": conv, "failed": int(np.sum(status == 2)),
+        "roofline": {"bound": "alu", "kernel": "dense_update", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_kind": ("measured FP64" if args.lu == "fp64" else "measured FP32")
+                     + " FMA-chain throughput (pf_fma_peak)",
+                     "traffic_kind": "ncu DRAM bytes per average active launch, scaled from a batch-640 capture",
+                     "launches": du[0], "ms_total": du[2]},
+        "hbm_roofline": {"algorithmic_bytes_per_instance_iteration": bmin,
+                         "achieved_gbs": step_bytes * args.steps / (ms_max / 1e3) / 1e9,
+                         "peak_gbs": hbm, "peak_kind": hbm_kind, "pct": hbm_pct},
+        "kernel_ms": {k: round(v[2], 3) for k, v in prof.items() if v[1] > 0},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -161,6 +161,36 @@ int pf_stage_factor(pf_plan* p, int B, const double* v, int factor, double* lu_o
 int pf_stage_linear_solve(pf_plan* p, int B, const double* v, const double* rhs, double* dx,
                           void* stream);
 
+/* ---- launch accounting and per-kernel device time ----
+ * Kernel classes (index into the pf_profile arrays): 0 load (input transpose),
+ * 1 store, 2 mismatch_jacobian, 3 check, 4 zero_lu, 5 set_ones,
+ * 6 lu_sparse_level, 7 dense_diag, 8 dense_panel, 9 dense_update, 10 fwd_level,
+ * 11 dense_solve, 12 bwd_level, 13 update, 14 aux. */
+#define NRPF_KCLASSES 16
+typedef struct pf_profile {
+  int64_t launches[NRPF_KCLASSES];  /* kernels enqueued by pf_solve_batch        */
+  int64_t timed[NRPF_KCLASSES];     /* launches bracketed by CUDA events          */
+  double ms[NRPF_KCLASSES];         /* summed event time of the timed launches    */
+} pf_profile;
+
+/* Reset the counters of a plan.  Every later launch of a class whose bit is set
+ * in time_mask is bracketed by two CUDA events recorded on the launching
+ * stream (adds two event records per launch).  Not thread-safe. */
+int pf_profile_start(pf_plan* p, uint32_t time_mask);
+
+/* Wait for the recorded events (host-blocking) and report counts and times. */
+int pf_profile_read(pf_plan* p, pf_profile* out);
+
+/* Static name of a kernel class, or "unknown". */
+const char* pf_kernel_class_name(int c);
+
+/* Measured FP64 and FP32 fused-multiply-add throughput of the current device
+ * (TFLOP/s, 2 flop per FMA), the arithmetic roofline against which the
+ * solver's FP-bound kernels are reported.  The paper has no counterpart: it
+ * is a measurement aid.  Runs a few hundred milliseconds of synchronous work
+ * on the given stream and allocates a small scratch buffer. */
+int pf_fma_peak(double* fp64_tflops, double* fp32_tflops, void* stream);
+
 void pf_plan_destroy(pf_plan* p);
 
 /* Static string naming a return code (or "unknown"). */

@@ -37,15 +37,24 @@ class pf_plan_info(C.Structure):
                 ("capacity", C.c_int), ("lu_precision", C.c_int)]
 
 
+NKCLASSES = 16
+
+
+class pf_profile(C.Structure):
+    _fields_ = [("launches", C.c_int64 * NKCLASSES), ("timed", C.c_int64 * NKCLASSES),
+                ("ms", C.c_double * NKCLASSES)]
+
+
 EXPORTS = ["pf_options_default", "pf_ybus_from_branches", "pf_plan_create", "pf_plan_get_info",
            "pf_plan_get_pattern", "pf_solve_batch", "pf_stage_mismatch", "pf_stage_factor",
-           "pf_stage_linear_solve", "pf_plan_destroy", "pf_status_str"]
+           "pf_stage_linear_solve", "pf_profile_start", "pf_profile_read", "pf_kernel_class_name",
+           "pf_fma_peak", "pf_plan_destroy", "pf_status_str"]
 
 
 def _load():
     if not os.path.exists(LIB_PATH):
         raise NrpfError(f"{LIB_PATH} is missing: build it with "
-                        "`python -m paper_2101_02270_gb300.build` (no CPU fallback exists)")
+                        "`python paper_2101_02270_gb300/build.py` (no CPU fallback exists)")
     lib = C.CDLL(LIB_PATH)
     P, I, D, I64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
     lib.pf_options_default.argtypes = [C.POINTER(pf_options)]
@@ -57,6 +66,11 @@ def _load():
     lib.pf_stage_mismatch.argtypes = [P, I, P, P, P, P, P]
     lib.pf_stage_factor.argtypes = [P, I, P, I, P, P]
     lib.pf_stage_linear_solve.argtypes = [P, I, P, P, P, P]
+    lib.pf_profile_start.argtypes = [P, C.c_uint32]
+    lib.pf_profile_read.argtypes = [P, C.POINTER(pf_profile)]
+    lib.pf_kernel_class_name.argtypes = [I]
+    lib.pf_kernel_class_name.restype = C.c_char_p
+    lib.pf_fma_peak.argtypes = [C.POINTER(D), C.POINTER(D), P]
     lib.pf_plan_destroy.argtypes = [P]
     lib.pf_plan_destroy.restype = None
     lib.pf_status_str.argtypes = [I]
@@ -95,3 +109,10 @@ def ybus_from_branches(n, f, t, r, x, b):
                                     C.byref(nnz)), "pf_ybus_from_branches")
     k = nnz.value
     return rowptr, colidx[:k].copy(), yre[:k].copy(), yim[:k].copy()
+
+
+def fma_peak(stream=None):
+    """(fp64, fp32) FMA throughput of the current device in TFLOP/s."""
+    a, b = C.c_double(0), C.c_double(0)
+    check(lib.pf_fma_peak(C.byref(a), C.byref(b), stream), "pf_fma_peak")
+    return a.value, b.value

@@ -1,7 +1,8 @@
 """Build the in-tree shared library ``libnrpf.so`` (CUDA for sm_103a + host C++).
 
 Each translation unit is compiled in parallel by nvcc, then linked with the
-static CUDA runtime.  Usage: ``python -m paper_2101_02270_gb300.build``.
+static CUDA runtime.  Usage: ``python paper_2101_02270_gb300/build.py`` (run as a script: importing the
+package itself needs the built library).
 """
 from __future__ import annotations
 
@@ -16,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "kernels.cu", "plan.cpp", "ordering.cpp"]
+SOURCES = ["api.cu", "kernels.cu", "peak.cu", "plan.cpp", "ordering.cpp"]
 
 
 def _nvcc() -> str:

@@ -32,7 +32,7 @@ struct pf_plan {
   std::vector<void*> ws_allocs;
   int64_t* d_pattern_map = nullptr;  // CCS pattern -> LU element
   int64_t pattern_nnz = 0;
-  std::string last_error;
+  nrpf::Recorder rec;
 };
 
 namespace {
@@ -114,23 +114,24 @@ void enqueue_solve(pf_plan* p, int B, const double* sbus, const double* v0, doub
   const DevPlan& P = p->dp;
   const DevState& S = p->st;
   const HostPlan& h = p->hp;
-  nrpf::launch_load(P, S, B, sbus, v0, st);
+  nrpf::Recorder* rec = &p->rec;
+  nrpf::launch_load(P, S, B, sbus, v0, st, rec);
   cudaMemsetAsync(S.n_active, 0, 2 * sizeof(int32_t), st);
   for (int it = 0; it <= maxit; ++it) {
     int32_t* counter = S.n_active + (it & 1);
     const int32_t* prev = it == 0 ? nullptr : S.n_active + ((it - 1) & 1);
     if (P.m > 0) {
-      nrpf::launch_prepare_lu<T>(P, S, prev, st);
-      nrpf::launch_mismatch<T>(P, S, 1, prev, st);
+      nrpf::launch_prepare_lu<T>(P, S, prev, st, rec);
+      nrpf::launch_mismatch<T>(P, S, 1, prev, st, rec);
     }
     cudaMemsetAsync(counter, 0, sizeof(int32_t), st);
-    nrpf::launch_check(S, it, maxit, tol, counter, st);
+    nrpf::launch_check(S, it, maxit, tol, counter, st, rec);
     if (it == maxit || P.m == 0) break;
-    nrpf::launch_factor<T>(P, S, h.lu_lvl_ptr, counter, st);
-    nrpf::launch_solve<T>(P, S, h.fw_lvl_ptr, h.bw_lvl_ptr, counter, st);
-    nrpf::launch_update<T>(P, S, counter, st);
+    nrpf::launch_factor<T>(P, S, h.lu_lvl_ptr, counter, st, rec);
+    nrpf::launch_solve<T>(P, S, h.fw_lvl_ptr, h.bw_lvl_ptr, counter, st, rec);
+    nrpf::launch_update<T>(P, S, counter, st, rec);
   }
-  nrpf::launch_store(P, S, B, v_out, iters, status, st);
+  nrpf::launch_store(P, S, B, v_out, iters, status, st, rec);
 }
 
 int build_pattern_map(pf_plan* p) {
@@ -417,6 +418,32 @@ int pf_stage_linear_solve(pf_plan* p, int B, const double* v, const double* rhs,
     nrpf::launch_rhs_out<double>(p->dp, p->st, B, dx, st);
   }
   return check_launch();
+}
+
+int pf_profile_start(pf_plan* p, uint32_t time_mask) {
+  if (!p || p->host_only) return NRPF_ERR_ARG;
+  p->rec.reset(time_mask);
+  return NRPF_OK;
+}
+
+int pf_profile_read(pf_plan* p, pf_profile* out) {
+  if (!p || !out || p->host_only) return NRPF_ERR_ARG;
+  p->rec.drain();
+  static_assert(nrpf::K_NCLASS <= NRPF_KCLASSES, "kernel class table too small");
+  for (int c = 0; c < NRPF_KCLASSES; ++c) {
+    out->launches[c] = c < nrpf::K_NCLASS ? p->rec.launches[c] : 0;
+    out->timed[c] = c < nrpf::K_NCLASS ? p->rec.timed[c] : 0;
+    out->ms[c] = c < nrpf::K_NCLASS ? p->rec.ms[c] : 0.0;
+  }
+  return check_launch();
+}
+
+const char* pf_kernel_class_name(int c) {
+  static const char* names[] = {"load", "store", "mismatch_jacobian", "check", "zero_lu", "set_ones",
+                                "lu_sparse_level", "dense_diag", "dense_panel", "dense_update", "fwd_level",
+                                "dense_solve", "bwd_level", "update", "aux"};
+  if (c < 0 || c >= nrpf::K_NCLASS) return "unknown";
+  return names[c];
 }
 
 void pf_plan_destroy(pf_plan* p) {

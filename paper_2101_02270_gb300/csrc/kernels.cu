@@ -588,101 +588,110 @@ __global__ void k_lu_out(DevPlan P, DevState S, int B, const int64_t* __restrict
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// Host-side launchers
+// Host-side launchers (every launch goes through NRPF_LAUNCH for counting and
+// optional per-class CUDA-event timing)
 // ---------------------------------------------------------------------------
 static inline dim3 grid2(int64_t items, int per_block, int tiles) {
   return dim3((unsigned)((items + per_block - 1) / per_block), (unsigned)tiles);
 }
 
 void launch_load(const DevPlan& P, const DevState& S, int B, const double* sbus, const double* v0,
-                 cudaStream_t st) {
+                 cudaStream_t st, Recorder* rec) {
   dim3 g((P.n + 31) / 32, S.Bp / kTile);
-  k_load<<<g, dim3(32, 8), 0, st>>>(P, S, B, reinterpret_cast<const double2*>(sbus),
-                                    reinterpret_cast<const double2*>(v0));
+  NRPF_LAUNCH(rec, K_LOAD, st,
+              k_load<<<g, dim3(32, 8), 0, st>>>(P, S, B, reinterpret_cast<const double2*>(sbus),
+                                                reinterpret_cast<const double2*>(v0)));
 }
 
 void launch_store(const DevPlan& P, const DevState& S, int B, double* v_out, int32_t* iters,
-                  uint8_t* status, cudaStream_t st) {
+                  uint8_t* status, cudaStream_t st, Recorder* rec) {
   dim3 g((P.n + 31) / 32, S.Bp / kTile);
-  k_store<<<g, dim3(32, 8), 0, st>>>(P, S, B, reinterpret_cast<double2*>(v_out), iters, status);
+  NRPF_LAUNCH(rec, K_STORE, st,
+              k_store<<<g, dim3(32, 8), 0, st>>>(P, S, B, reinterpret_cast<double2*>(v_out), iters, status));
 }
 
 template <typename T>
-void launch_mismatch(const DevPlan& P, const DevState& S, int jac, const int32_t* gate, cudaStream_t st) {
+void launch_mismatch(const DevPlan& P, const DevState& S, int jac, const int32_t* gate, cudaStream_t st,
+                     Recorder* rec) {
   dim3 g((P.n + kMWarps * kBusPerWarp - 1) / (kMWarps * kBusPerWarp), S.Bp / kTile);
-  k_mismatch_jac<T><<<g, dim3(32, kMWarps), 0, st>>>(P, S, jac, gate);
+  NRPF_LAUNCH(rec, K_MISMATCH, st, k_mismatch_jac<T><<<g, dim3(32, kMWarps), 0, st>>>(P, S, jac, gate));
 }
 
-void launch_check(const DevState& S, int it, int maxit, double tol, int32_t* counter, cudaStream_t st) {
-  k_check<<<(S.Bp + 255) / 256, 256, 0, st>>>(S, S.Bp, it, maxit, tol, counter);
+void launch_check(const DevState& S, int it, int maxit, double tol, int32_t* counter, cudaStream_t st,
+                  Recorder* rec) {
+  NRPF_LAUNCH(rec, K_CHECK, st,
+              k_check<<<(S.Bp + 255) / 256, 256, 0, st>>>(S, S.Bp, it, maxit, tol, counter));
 }
 
 template <typename T>
-void launch_prepare_lu(const DevPlan& P, const DevState& S, const int32_t* gate, cudaStream_t st) {
+void launch_prepare_lu(const DevPlan& P, const DevState& S, const int32_t* gate, cudaStream_t st,
+                       Recorder* rec) {
   const size_t n16 = (size_t)P.NLU * S.Bp * sizeof(T) / 16;  // NLU*Bp*sizeof(T) is a multiple of 128
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_zero16<<<sms * 8, 256, 0, st>>>(reinterpret_cast<uint4*>(S.lu), n16, gate);
-  if (P.n_one > 0) k_set_ones<T><<<dim3(1, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate);
+  NRPF_LAUNCH(rec, K_ZERO, st, k_zero16<<<sms * 8, 256, 0, st>>>(reinterpret_cast<uint4*>(S.lu), n16, gate));
+  if (P.n_one > 0)
+    NRPF_LAUNCH(rec, K_ONES, st, k_set_ones<T><<<dim3(1, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate));
+}
+
+template <typename T, int KB>
+static void launch_dense_step(const DevPlan& P, const DevState& S, int k, const int32_t* gate, cudaStream_t st,
+                              Recorder* rec) {
+  const int tiles = S.Bp / kTile;
+  const int rem = P.ndp - k - KB;
+  NRPF_LAUNCH(rec, K_DENSE_DIAG, st,
+              k_dense_diag<T, KB><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, k, gate));
+  if (rem > 0) {
+    NRPF_LAUNCH(rec, K_DENSE_PANEL, st,
+                k_dense_panel<T, KB><<<grid2(2 * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate));
+    NRPF_LAUNCH(rec, K_DENSE_UPDATE, st,
+                k_dense_update<T, KB><<<grid2((int64_t)(rem / 4) * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(
+                    P, S, k, gate));
+  }
 }
 
 template <typename T>
 void launch_factor(const DevPlan& P, const DevState& S, const std::vector<int32_t>& lvl_ptr,
-                   const int32_t* gate, cudaStream_t st) {
+                   const int32_t* gate, cudaStream_t st, Recorder* rec) {
   const int tiles = S.Bp / kTile;
   for (size_t l = 0; l + 1 < lvl_ptr.size(); ++l) {
     int c0 = lvl_ptr[l], c1 = lvl_ptr[l + 1];
     if (c1 <= c0) continue;
-    k_lu_sparse_level<T><<<grid2(c1 - c0, kLWarps, tiles), dim3(32, kLWarps), 0, st>>>(P, S, c0, c1, gate);
+    NRPF_LAUNCH(rec, K_LU_SPARSE, st,
+                k_lu_sparse_level<T><<<grid2(c1 - c0, kLWarps, tiles), dim3(32, kLWarps), 0, st>>>(P, S, c0, c1,
+                                                                                                  gate));
   }
-  const int ld = P.ndp;
-  for (int k = 0; k < ld; k += P.kb) {
-    const int rem = ld - k - P.kb;
-    switch (P.kb) {
-      case 4:
-        k_dense_diag<T, 4><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, k, gate);
-        if (rem > 0) {
-          k_dense_panel<T, 4><<<grid2(2 * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
-          k_dense_update<T, 4><<<grid2((int64_t)(rem / 4) * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
-        }
-        break;
-      case 8:
-        k_dense_diag<T, 8><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, k, gate);
-        if (rem > 0) {
-          k_dense_panel<T, 8><<<grid2(2 * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
-          k_dense_update<T, 8><<<grid2((int64_t)(rem / 4) * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
-        }
-        break;
-      default:
-        k_dense_diag<T, 16><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, k, gate);
-        if (rem > 0) {
-          k_dense_panel<T, 16><<<grid2(2 * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
-          k_dense_update<T, 16><<<grid2((int64_t)(rem / 4) * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate);
-        }
-        break;
-    }
+  for (int k = 0; k < P.ndp; k += P.kb) {
+    if (P.kb == 4) launch_dense_step<T, 4>(P, S, k, gate, st, rec);
+    else if (P.kb == 8) launch_dense_step<T, 8>(P, S, k, gate, st, rec);
+    else launch_dense_step<T, 16>(P, S, k, gate, st, rec);
   }
 }
 
 template <typename T>
 void launch_solve(const DevPlan& P, const DevState& S, const std::vector<int32_t>& fw_lvl,
-                  const std::vector<int32_t>& bw_lvl, const int32_t* gate, cudaStream_t st) {
+                  const std::vector<int32_t>& bw_lvl, const int32_t* gate, cudaStream_t st, Recorder* rec) {
   const int tiles = S.Bp / kTile;
   for (size_t l = 0; l + 1 < fw_lvl.size(); ++l) {
     int r0 = fw_lvl[l], r1 = fw_lvl[l + 1];
-    if (r1 > r0) k_fwd_level<T><<<grid2(r1 - r0, 4, tiles), dim3(32, 4), 0, st>>>(P, S, r0, r1, gate);
+    if (r1 > r0)
+      NRPF_LAUNCH(rec, K_FWD, st,
+                  k_fwd_level<T><<<grid2(r1 - r0, 4, tiles), dim3(32, 4), 0, st>>>(P, S, r0, r1, gate));
   }
-  if (P.ndp > 0) k_dense_solve<T><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, gate);
+  if (P.ndp > 0)
+    NRPF_LAUNCH(rec, K_DENSE_SOLVE, st, k_dense_solve<T><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, gate));
   for (size_t l = 0; l + 1 < bw_lvl.size(); ++l) {
     int r0 = bw_lvl[l], r1 = bw_lvl[l + 1];
-    if (r1 > r0) k_bwd_level<T><<<grid2(r1 - r0, 4, tiles), dim3(32, 4), 0, st>>>(P, S, r0, r1, gate);
+    if (r1 > r0)
+      NRPF_LAUNCH(rec, K_BWD, st,
+                  k_bwd_level<T><<<grid2(r1 - r0, 4, tiles), dim3(32, 4), 0, st>>>(P, S, r0, r1, gate));
   }
 }
 
 template <typename T>
-void launch_update(const DevPlan& P, const DevState& S, const int32_t* gate, cudaStream_t st) {
-  k_update<T><<<grid2(P.n, 8, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate);
+void launch_update(const DevPlan& P, const DevState& S, const int32_t* gate, cudaStream_t st, Recorder* rec) {
+  NRPF_LAUNCH(rec, K_UPDATE, st, k_update<T><<<grid2(P.n, 8, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate));
 }
 
 template <typename T>
@@ -707,18 +716,20 @@ void launch_lu_out(const DevPlan& P, const DevState& S, int B, const int64_t* ma
   if (nnz > 0) k_lu_out<T><<<grid2(nnz, 8, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, B, map, nnz, out);
 }
 
-#define NRPF_INST(T)                                                                                        \
-  template void launch_mismatch<T>(const DevPlan&, const DevState&, int, const int32_t*, cudaStream_t);    \
-  template void launch_prepare_lu<T>(const DevPlan&, const DevState&, const int32_t*, cudaStream_t);       \
-  template void launch_factor<T>(const DevPlan&, const DevState&, const std::vector<int32_t>&,             \
-                                 const int32_t*, cudaStream_t);                                            \
-  template void launch_solve<T>(const DevPlan&, const DevState&, const std::vector<int32_t>&,              \
-                                const std::vector<int32_t>&, const int32_t*, cudaStream_t);                \
-  template void launch_update<T>(const DevPlan&, const DevState&, const int32_t*, cudaStream_t);           \
-  template void launch_rhs_in<T>(const DevPlan&, const DevState&, int, const double*, cudaStream_t);       \
-  template void launch_rhs_out<T>(const DevPlan&, const DevState&, int, double*, cudaStream_t);            \
-  template void launch_f_out<T>(const DevPlan&, const DevState&, int, double*, double*, cudaStream_t);     \
-  template void launch_lu_out<T>(const DevPlan&, const DevState&, int, const int64_t*, int64_t, double*,   \
+#define NRPF_INST(T)                                                                                          \
+  template void launch_mismatch<T>(const DevPlan&, const DevState&, int, const int32_t*, cudaStream_t,       \
+                                   Recorder*);                                                               \
+  template void launch_prepare_lu<T>(const DevPlan&, const DevState&, const int32_t*, cudaStream_t,          \
+                                     Recorder*);                                                             \
+  template void launch_factor<T>(const DevPlan&, const DevState&, const std::vector<int32_t>&,               \
+                                 const int32_t*, cudaStream_t, Recorder*);                                   \
+  template void launch_solve<T>(const DevPlan&, const DevState&, const std::vector<int32_t>&,                \
+                                const std::vector<int32_t>&, const int32_t*, cudaStream_t, Recorder*);       \
+  template void launch_update<T>(const DevPlan&, const DevState&, const int32_t*, cudaStream_t, Recorder*);  \
+  template void launch_rhs_in<T>(const DevPlan&, const DevState&, int, const double*, cudaStream_t);         \
+  template void launch_rhs_out<T>(const DevPlan&, const DevState&, int, double*, cudaStream_t);              \
+  template void launch_f_out<T>(const DevPlan&, const DevState&, int, double*, double*, cudaStream_t);       \
+  template void launch_lu_out<T>(const DevPlan&, const DevState&, int, const int64_t*, int64_t, double*,     \
                                  cudaStream_t);
 
 NRPF_INST(double)

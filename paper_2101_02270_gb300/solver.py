@@ -13,6 +13,7 @@ from ._lib import check, lib
 
 _PREC = {"fp64": _lib.LU_FP64, "fp32": _lib.LU_FP32}
 _ORDER = {"amd": _lib.ORDER_AMD, "natural": _lib.ORDER_NATURAL}
+KERNEL_CLASSES = [lib.pf_kernel_class_name(i).decode() for i in range(15)]
 
 
 def _dptr(t: torch.Tensor) -> C.c_void_p:
@@ -143,6 +144,20 @@ class Plan:
         check(lib.pf_stage_linear_solve(self._h, B, _dptr(v), _dptr(rhs), _dptr(dx), _stream()),
               "pf_stage_linear_solve")
         return dx
+
+    # ---- launch accounting ----
+    def profile_start(self, time_classes=()):
+        """Reset launch counters; the named kernel classes get CUDA-event timing."""
+        mask = 0
+        for c in time_classes:
+            mask |= 1 << KERNEL_CLASSES.index(c)
+        check(lib.pf_profile_start(self._h, mask), "pf_profile_start")
+
+    def profile_read(self) -> dict:
+        """{class: (launches, timed launches, summed ms)} since profile_start."""
+        pr = _lib.pf_profile()
+        check(lib.pf_profile_read(self._h, C.byref(pr)), "pf_profile_read")
+        return {c: (pr.launches[i], pr.timed[i], pr.ms[i]) for i, c in enumerate(KERNEL_CLASSES)}
 
     def _check_bn(self, t, B):
         if t.dtype != torch.complex128 or t.shape != (B, self.n):
