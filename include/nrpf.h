@@ -191,6 +191,37 @@ const char* pf_kernel_class_name(int c);
  * on the given stream and allocates a small scratch buffer. */
 int pf_fma_peak(double* fp64_tflops, double* fp32_tflops, void* stream);
 
+/* Mismatch and max|F| of a batch without allocating device memory.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc when they evaluate the mismatch - code whose device memory is
+ * owned entirely by another allocator (a framework's caching pool holding the
+ * GPU), or a real-time loop that must not take cudaMalloc's latency and its
+ * implicit device-wide synchronisation.  pf_stage_mismatch computes the same
+ * values but stages them through the plan's workspace, which it grows with
+ * cudaMalloc when the batch exceeds the plan's capacity.
+ * Here the only scratch (the running per-instance maxima of the cross-block
+ * reduction and an arrival counter) lives in one static device array of
+ * NRPF_NOALLOC_MAX_BATCH + 32 eight-byte words (about 512 KB), which every GPU
+ * that loads the library holds until the process exits.
+ * device in : sbus, v [B,n] complex as in pf_solve_batch.
+ * device out: F [B,m] float64, row r = the equation at position r of
+ *             A = P J P^T (pf_plan_get_pattern's pos_of_unknown maps J row u to
+ *             position pos_of_unknown[u]); norm [B] = max |F| (a non-finite
+ *             entry gives +inf).
+ * The first call on a device looks up the array's device address (a runtime
+ * query, once per device, with that device current); make that first call
+ * before any stream capture begins.  Each call clears the part of the array it
+ * uses (stream-ordered memsets) and then runs one kernel.  All calls share the
+ * array, so calls that overlap on the GPU (different streams, or threads)
+ * race and give wrong norms: serialise them.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.
+ * Errors: NRPF_ERR_ARG (null pointers, host-only plan, B < 0),
+ * NRPF_ERR_CAPACITY (B > NRPF_NOALLOC_MAX_BATCH), NRPF_ERR_CUDA.
+ * B == 0 is a no-op. */
+#define NRPF_NOALLOC_MAX_BATCH 65536
+int pf_stage_mismatch_noalloc(const pf_plan* p, int B, const double* sbus, const double* v, double* F,
+                              double* norm, void* stream);
+
 void pf_plan_destroy(pf_plan* p);
 
 /* Static string naming a return code (or "unknown"). */

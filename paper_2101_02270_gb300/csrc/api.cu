@@ -12,6 +12,7 @@
 
 #include "../../include/nrpf.h"
 #include "device.h"
+#include "handle.h"
 #include "kernels.h"
 #include "plan.h"
 
@@ -20,20 +21,6 @@ using nrpf::DevState;
 using nrpf::HostPlan;
 using nrpf::kTile;
 
-struct pf_plan {
-  HostPlan hp;
-  DevPlan dp{};
-  DevState st{};
-  int capacity = 0;  // instances (multiple of kTile)
-  int lu_precision = NRPF_LU_FP64;
-  int device = 0;
-  int host_only = 0;
-  std::vector<void*> plan_allocs;
-  std::vector<void*> ws_allocs;
-  int64_t* d_pattern_map = nullptr;  // CCS pattern -> LU element
-  int64_t pattern_nnz = 0;
-  nrpf::Recorder rec;
-};
 
 namespace {
 

@@ -1,0 +1,25 @@
+// The opaque plan handle of the C ABI (internal definition, shared by the
+// translation units that implement entry points).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "../../include/nrpf.h"
+#include "device.h"
+#include "plan.h"
+#include "recorder.h"
+
+struct pf_plan {
+  nrpf::HostPlan hp;
+  nrpf::DevPlan dp{};
+  nrpf::DevState st{};
+  int capacity = 0;  // instances (multiple of kTile)
+  int lu_precision = NRPF_LU_FP64;
+  int device = 0;
+  int host_only = 0;
+  std::vector<void*> plan_allocs;
+  std::vector<void*> ws_allocs;
+  int64_t* d_pattern_map = nullptr;  // CCS pattern -> LU element
+  int64_t pattern_nnz = 0;
+  nrpf::Recorder rec;
+};
