@@ -496,6 +496,74 @@ __global__ void k_dense_solve(DevPlan P, DevState S, const int32_t* __restrict__
   }
 }
 
+// Dense block solves with one tile's right-hand side held in shared memory.
+// CTA = one tile (32 instances) x kSolveWarps warps.  Forward (unit lower) and
+// backward (upper) substitution by blocks of SB columns: warp 0 solves the
+// SB x SB diagonal block, then every warp updates its share of the remaining
+// rows with SB multiply-adds each (the row updates of a block are independent).
+constexpr int kSolveWarps = 4;
+
+template <typename T, int SB>
+__global__ void __launch_bounds__(32 * kSolveWarps) k_dense_solve_smem(DevPlan P, DevState S,
+                                                                       const int32_t* __restrict__ gate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);  // [ndp][32]
+  if (gate && *gate == 0) return;
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int tile = blockIdx.x;
+  if (!__syncthreads_or(S.active[tile * kTile + lane])) return;
+  const T* __restrict__ A = reinterpret_cast<const T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
+  T* __restrict__ X = reinterpret_cast<T*>(S.x) + ((size_t)tile * P.mp + P.s) * kTile + lane;
+  const int ld = P.ndp;
+  for (int r = warp; r < ld; r += kSolveWarps) xs[r * kTile + lane] = X[(size_t)r * kTile];
+  __syncthreads();
+  for (int k0 = 0; k0 < ld; k0 += SB) {
+    if (warp == 0) {
+#pragma unroll
+      for (int c = 0; c < SB; ++c) {
+        const T xc = xs[(k0 + c) * kTile + lane];
+#pragma unroll
+        for (int r = c + 1; r < SB; ++r)
+          xs[(k0 + r) * kTile + lane] -= A[((size_t)(k0 + c) * ld + k0 + r) * kTile] * xc;
+      }
+    }
+    __syncthreads();
+    T xb[SB];
+#pragma unroll
+    for (int c = 0; c < SB; ++c) xb[c] = xs[(k0 + c) * kTile + lane];
+    for (int r = k0 + SB + warp; r < ld; r += kSolveWarps) {
+      T acc = xs[r * kTile + lane];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) acc -= A[((size_t)(k0 + c) * ld + r) * kTile] * xb[c];
+      xs[r * kTile + lane] = acc;
+    }
+    __syncthreads();
+  }
+  for (int k0 = ld - SB; k0 >= 0; k0 -= SB) {
+    if (warp == 0) {
+#pragma unroll
+      for (int c = SB - 1; c >= 0; --c) {
+        const T xc = xs[(k0 + c) * kTile + lane] / A[((size_t)(k0 + c) * ld + k0 + c) * kTile];
+        xs[(k0 + c) * kTile + lane] = xc;
+#pragma unroll
+        for (int r = 0; r < c; ++r) xs[(k0 + r) * kTile + lane] -= A[((size_t)(k0 + c) * ld + k0 + r) * kTile] * xc;
+      }
+    }
+    __syncthreads();
+    T xb[SB];
+#pragma unroll
+    for (int c = 0; c < SB; ++c) xb[c] = xs[(k0 + c) * kTile + lane];
+    for (int r = warp; r < k0; r += kSolveWarps) {
+      T acc = xs[r * kTile + lane];
+#pragma unroll
+      for (int c = 0; c < SB; ++c) acc -= A[((size_t)(k0 + c) * ld + r) * kTile] * xb[c];
+      xs[r * kTile + lane] = acc;
+    }
+    __syncthreads();
+  }
+  for (int r = warp; r < ld; r += kSolveWarps) X[(size_t)r * kTile] = xs[r * kTile + lane];
+}
+
 // ---------------------------------------------------------------------------
 // Voltage update (Sec. 3, step 4): th[PV+PQ] += dx, |V|[PQ] += dx, then the
 // rectangular form and 1/|V| for the next mismatch.  Inactive instances keep
@@ -669,6 +737,24 @@ void launch_factor(const DevPlan& P, const DevState& S, const std::vector<int32_
   }
 }
 
+// Dense solve with the tile's right-hand side in shared memory, when it fits.
+constexpr size_t kSolveSmemMax = 200 * 1024;
+
+template <typename T, int SB>
+static void launch_dense_solve_smem(const DevPlan& P, const DevState& S, const int32_t* gate, cudaStream_t st,
+                                    Recorder* rec, size_t smem) {
+  static bool configured[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !configured[dev]) {
+    cudaFuncSetAttribute(k_dense_solve_smem<T, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSolveSmemMax);
+    if (dev >= 0 && dev < 64) configured[dev] = true;
+  }
+  NRPF_LAUNCH(rec, K_DENSE_SOLVE, st,
+              k_dense_solve_smem<T, SB><<<S.Bp / kTile, dim3(32, kSolveWarps), smem, st>>>(P, S, gate));
+}
+
 template <typename T>
 void launch_solve(const DevPlan& P, const DevState& S, const std::vector<int32_t>& fw_lvl,
                   const std::vector<int32_t>& bw_lvl, const int32_t* gate, cudaStream_t st, Recorder* rec) {
@@ -679,8 +765,18 @@ void launch_solve(const DevPlan& P, const DevState& S, const std::vector<int32_t
       NRPF_LAUNCH(rec, K_FWD, st,
                   k_fwd_level<T><<<grid2(r1 - r0, 4, tiles), dim3(32, 4), 0, st>>>(P, S, r0, r1, gate));
   }
-  if (P.ndp > 0)
-    NRPF_LAUNCH(rec, K_DENSE_SOLVE, st, k_dense_solve<T><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, gate));
+  if (P.ndp > 0) {
+    const size_t smem = (size_t)P.ndp * kTile * sizeof(T);
+    if (smem <= kSolveSmemMax) {
+      if (P.ndp % 8 == 0)
+        launch_dense_solve_smem<T, 8>(P, S, gate, st, rec, smem);
+      else
+        launch_dense_solve_smem<T, 4>(P, S, gate, st, rec, smem);
+    } else {
+      NRPF_LAUNCH(rec, K_DENSE_SOLVE, st,
+                  k_dense_solve<T><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, gate));
+    }
+  }
   for (size_t l = 0; l + 1 < bw_lvl.size(); ++l) {
     int r0 = bw_lvl[l], r1 = bw_lvl[l + 1];
     if (r1 > r0)
