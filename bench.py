@@ -56,7 +56,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="mesh2000_b10k", choices=list(gridgen.CONFIGS))
+    ap.add_argument("--config", default="mesh2000_b10k", choices=list(gridgen.CONFIGS) + ["feeders256x100"])
     ap.add_argument("--batch", type=int, default=0, help="override the batch size (0 = the workload's)")
     ap.add_argument("--lu", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--maxit", type=int, default=MAXIT)
@@ -181,6 +181,96 @@ def dense_update_flop(ndp, kb):
         if r > 0:
             tot += 2 * r * r * kb
     return tot
+
+
+def run_feeders(args):
+    """256 radial feeders of 20-400 buses, 100 scenarios each, every feeder
+    with its own pattern and plan, solved by one persistent graph-captured
+    launch (pf_multi_solve) whose shape the library's autotuner picks."""
+    import torch
+
+    import paper_2101_02270_gb300 as pf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    fs = gridgen.make_feeders()
+    scen = gridgen.grids.feeder_scenarios(fs, seed=1 + rank)
+    S = np.concatenate([sc.sbus(g).ravel() for g, sc in zip(fs, scen)])
+    V0 = np.concatenate([sc.v0_flat(g).ravel() for g, sc in zip(fs, scen)])
+    lu = "fp32" if args.lu == "fp64" and not args.lu_explicit else args.lu
+    t0 = time.perf_counter()
+    plans = [pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision=lu, dense_frac=1.0)
+             for g in fs]
+    mp = pf.MultiPlan(plans, [sc.batch for sc in scen])
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    Sd = torch.from_numpy(S).to(dev)
+    Vd = torch.from_numpy(V0).to(dev)
+    maxit = args.maxit if args.maxit != MAXIT else 20
+    tuned = mp.autotune(Sd, Vd, TOL, maxit)
+    out = mp._outs(Sd)
+    for _ in range(max(args.warmup, 0)):
+        mp.solve(Sd, Vd, TOL, maxit, out=out)
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        mp.solve(Sd, Vd, TOL, maxit, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    it = out[1].cpu().numpy()
+    st = out[2].cpu().numpy()
+    conv = int(np.sum(st == 0))
+    value = conv * args.steps / (ms / 1e3)
+    # end to end from pinned host buffers
+    S_h, V_h = torch.from_numpy(S).pin_memory(), torch.from_numpy(V0).pin_memory()
+    Vo_h = torch.empty_like(S_h).pin_memory()
+    it_h = torch.empty(mp.total, dtype=torch.int32).pin_memory()
+    st_h = torch.empty(mp.total, dtype=torch.uint8).pin_memory()
+    S2, V2 = torch.empty_like(Sd), torch.empty_like(Vd)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        S2.copy_(S_h, non_blocking=True)
+        V2.copy_(V_h, non_blocking=True)
+        v, i2, s2 = mp.solve(S2, V2, TOL, maxit, out=out)
+        Vo_h.copy_(v, non_blocking=True)
+        it_h.copy_(i2, non_blocking=True)
+        st_h.copy_(s2, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e = int(np.sum(st_h.numpy() == 0)) * args.steps / (e0.elapsed_time(e1) / 1e3)
+    nbus = np.array([g.n for g in fs])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32lu" if lu == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "feeders256x100", "feeders": len(fs), "scenarios_per_feeder": 100,
+                   "buses_min": int(nbus.min()), "buses_max": int(nbus.max()), "buses_total": int(nbus.sum()),
+                   "lu_precision": lu, "tol": TOL, "maxit": maxit, "load_scale": fs[0].load_scale,
+                   "launch": "one persistent kernel per solve, CUDA graph", "autotuned": tuned,
+                   "plan_ms": round(plan_ms, 1)},
+        "iterations": {"mean": float(it.mean()), "max": int(it.max()), "hist": np.bincount(it).tolist()},
+        "converged": conv, "failed": int(np.sum(st == 2)),
+        "clocks": clk,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(2 * S.nbytes),
+                "d2h_bytes_per_step": int(S.nbytes + 5 * mp.total)},
+        "gpu_launches": 1,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    mp.close()
 
 
 def run_ours(args):
@@ -340,8 +430,11 @@ def run_ours(args):
 
 def main():
     args = parse_args()
+    args.lu_explicit = "--lu" in sys.argv
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "feeders256x100":
+        run_feeders(args)
     else:
         run_ours(args)
 

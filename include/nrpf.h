@@ -161,6 +161,43 @@ int pf_stage_factor(pf_plan* p, int B, const double* v, int factor, double* lu_o
 int pf_stage_linear_solve(pf_plan* p, int B, const double* v, const double* rhs, double* dx,
                           void* stream);
 
+/* ---- uneven batching: many plans, one persistent launch ----
+ * Grids of different sizes and sparsity patterns (one plan each, all with the
+ * same LU precision and no dense block, i.e. created with dense_frac >= 1) and
+ * different scenario counts are solved together by one persistent kernel
+ * (the paper's remark on imbalanced batches across streams/GPUs, Sec. 5,
+ * motivates it).  Work items are (plan, tile of up to 32 scenarios), sorted
+ * by decreasing work and pulled from a device counter; each item runs the
+ * full Newton loop of Sec. 3 in a private workspace slot.  The launch is
+ * captured in a CUDA graph and replayed while arguments are unchanged. */
+typedef struct pf_multi pf_multi;
+
+/* host in: k plans (kept alive by the caller while the group exists) and
+ * batch[k] scenario counts.  Inputs and outputs of pf_multi_solve are the
+ * plans' [B_f, n_f] blocks concatenated in plan order; iters/status are
+ * concatenated [B_f] blocks.  Allocates the group's device tables and slots.
+ * Errors: NRPF_ERR_ARG (mixed precision, a plan with a dense block, host-only
+ * plan), NRPF_ERR_NOMEM, NRPF_ERR_CUDA. */
+int pf_multi_create(int k, pf_plan* const* plans, const int32_t* batch, pf_multi** out);
+
+/* Solve every scenario of the group (same semantics and outputs as
+ * pf_solve_batch, concatenated).  Asynchronous on stream. */
+int pf_multi_solve(pf_multi* mp, const double* sbus, const double* v0, double tol, int maxit, double* v_out,
+                   int32_t* iters, uint8_t* status, void* stream);
+
+/* Launch shape: warps per item (threads per instance, 1..16) and resident
+ * CTAs per SM (1..32); may grow the slot pool (allocation). */
+int pf_multi_set_config(pf_multi* mp, int warps, int blocks_per_sm);
+int pf_multi_get_config(const pf_multi* mp, int* warps, int* blocks_per_sm, int64_t* instances, int* items);
+
+/* Autotuner: times the real solve for every (warps, CTAs per SM) pair in
+ * {1,2,4,8,16}^2 with at most 2048 threads per SM, keeps the fastest and
+ * reports its time (host-blocking; outputs hold the last solve). */
+int pf_multi_autotune(pf_multi* mp, const double* sbus, const double* v0, double tol, int maxit, double* v_out,
+                      int32_t* iters, uint8_t* status, void* stream, double* best_ms);
+
+void pf_multi_destroy(pf_multi* mp);
+
 /* ---- launch accounting and per-kernel device time ----
  * Kernel classes (index into the pf_profile arrays): 0 load (input transpose),
  * 1 store, 2 mismatch_jacobian, 3 check, 4 zero_lu, 5 set_ones,

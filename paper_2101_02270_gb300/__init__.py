@@ -6,6 +6,6 @@ mismatch, Jacobian refill into a permuted LU workspace, sparse + dense LU
 refactorisation, forward/backward substitution and the voltage update.
 """
 from ._lib import NrpfError, lib, ybus_from_branches  # noqa: F401
-from .solver import Plan  # noqa: F401
+from .solver import MultiPlan, Plan  # noqa: F401
 
 STATUS = {0: "converged", 1: "maxit", 2: "failed"}

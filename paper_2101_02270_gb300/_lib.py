@@ -48,7 +48,9 @@ class pf_profile(C.Structure):
 EXPORTS = ["pf_options_default", "pf_ybus_from_branches", "pf_plan_create", "pf_plan_get_info",
            "pf_plan_get_pattern", "pf_solve_batch", "pf_stage_mismatch", "pf_stage_factor",
            "pf_stage_linear_solve", "pf_profile_start", "pf_profile_read", "pf_kernel_class_name",
-           "pf_fma_peak", "pf_stage_mismatch_noalloc", "pf_plan_destroy", "pf_status_str"]
+           "pf_fma_peak", "pf_stage_mismatch_noalloc", "pf_multi_create", "pf_multi_solve",
+           "pf_multi_set_config", "pf_multi_get_config", "pf_multi_autotune", "pf_multi_destroy",
+           "pf_plan_destroy", "pf_status_str"]
 
 
 def _load():
@@ -72,6 +74,13 @@ def _load():
     lib.pf_kernel_class_name.restype = C.c_char_p
     lib.pf_fma_peak.argtypes = [C.POINTER(D), C.POINTER(D), P]
     lib.pf_stage_mismatch_noalloc.argtypes = [P, I, P, P, P, P, P]
+    lib.pf_multi_create.argtypes = [I, P, P, C.POINTER(C.c_void_p)]
+    lib.pf_multi_solve.argtypes = [P, P, P, D, I, P, P, P, P]
+    lib.pf_multi_set_config.argtypes = [P, I, I]
+    lib.pf_multi_get_config.argtypes = [P, C.POINTER(I), C.POINTER(I), C.POINTER(I64), C.POINTER(I)]
+    lib.pf_multi_autotune.argtypes = [P, P, P, D, I, P, P, P, P, C.POINTER(D)]
+    lib.pf_multi_destroy.argtypes = [P]
+    lib.pf_multi_destroy.restype = None
     lib.pf_plan_destroy.argtypes = [P]
     lib.pf_plan_destroy.restype = None
     lib.pf_status_str.argtypes = [I]

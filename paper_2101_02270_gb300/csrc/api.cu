@@ -252,6 +252,9 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
   d.n = h.n; d.m = h.m; d.s = h.s; d.nd = h.nd; d.ndp = h.ndp; d.kb = h.kb; d.mp = h.s + h.ndp;
   d.NS = h.NS; d.NLU = h.NLU; d.nnzY = (int)h.colidx.size();
   d.n_one = (int)h.one_pos.size();
+  d.n_lu_lvl = (int)h.lu_lvl_ptr.size() - 1;
+  d.n_fw_lvl = (int)h.fw_lvl_ptr.size() - 1;
+  d.n_bw_lvl = (int)h.bw_lvl_ptr.size() - 1;
   std::vector<int32_t> ydiag(h.n);
   for (int i = 0; i < h.n; ++i)
     for (int q = h.rowptr[i]; q < h.rowptr[i + 1]; ++q)
@@ -270,7 +273,9 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
       (rc = upload(p, h.fw_ptr, &d.fw_ptr)) || (rc = upload(p, h.fw_pos, &d.fw_pos)) ||
       (rc = upload(p, h.fw_col, &d.fw_col)) || (rc = upload(p, h.bw_rows, &d.bw_rows)) ||
       (rc = upload(p, h.bw_ptr, &d.bw_ptr)) || (rc = upload(p, h.bw_pos, &d.bw_pos)) ||
-      (rc = upload(p, h.bw_col, &d.bw_col)) || (rc = upload(p, h.unk_pos, &d.unk_pos))) {
+      (rc = upload(p, h.bw_col, &d.bw_col)) || (rc = upload(p, h.unk_pos, &d.unk_pos)) ||
+      (rc = upload(p, h.lu_lvl_ptr, &d.lu_lvl_ptr)) || (rc = upload(p, h.fw_lvl_ptr, &d.fw_lvl_ptr)) ||
+      (rc = upload(p, h.bw_lvl_ptr, &d.bw_lvl_ptr))) {
     pf_plan_destroy(p);
     return rc;
   }

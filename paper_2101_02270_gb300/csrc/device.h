@@ -45,6 +45,10 @@ struct DevPlan {
   const int32_t* fw_rows; const int32_t* fw_ptr; const int32_t* fw_pos; const int32_t* fw_col;
   const int32_t* bw_rows; const int32_t* bw_ptr; const int32_t* bw_pos; const int32_t* bw_col;
   const int32_t* unk_pos;  // [m]
+  // level boundaries of the schedules (device copies, for fused kernels)
+  const int32_t* lu_lvl_ptr; int n_lu_lvl;
+  const int32_t* fw_lvl_ptr; int n_fw_lvl;
+  const int32_t* bw_lvl_ptr; int n_bw_lvl;
 };
 
 // Per-solve workspace (capacity Bp instances, a multiple of kTile).

@@ -162,3 +162,59 @@ class Plan:
     def _check_bn(self, t, B):
         if t.dtype != torch.complex128 or t.shape != (B, self.n):
             raise ValueError(f"expected complex128 [{B}, {self.n}], got {t.dtype} {tuple(t.shape)}")
+
+
+class MultiPlan:
+    """Uneven batch: several plans (no dense block) with their own scenario
+    counts, solved by one persistent, graph-captured launch (pf_multi_*)."""
+
+    def __init__(self, plans, batches):
+        self.plans = list(plans)
+        self.batches = [int(b) for b in batches]
+        arr = (C.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        bat = np.ascontiguousarray(self.batches, np.int32)
+        h = C.c_void_p()
+        check(lib.pf_multi_create(len(self.plans), arr, _lib._np_ptr(bat), C.byref(h)), "pf_multi_create")
+        self._h = h
+        self._keep = (arr, bat)
+        self.total = int(sum(self.batches))
+        self.sizes = [p.n for p in self.plans]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.pf_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _outs(self, sbus):
+        dev = sbus.device
+        return (torch.empty_like(sbus), torch.empty(self.total, dtype=torch.int32, device=dev),
+                torch.empty(self.total, dtype=torch.uint8, device=dev))
+
+    def solve(self, sbus, v0, tol=1e-8, maxit=10, out=None):
+        """sbus, v0: complex128 1-D tensors, the [B_f, n_f] blocks concatenated."""
+        v, it, st = out if out is not None else self._outs(sbus)
+        check(lib.pf_multi_solve(self._h, _dptr(sbus), _dptr(v0), float(tol), int(maxit), _dptr(v), _dptr(it),
+                                 _dptr(st), _stream()), "pf_multi_solve")
+        return v, it, st
+
+    def autotune(self, sbus, v0, tol=1e-8, maxit=10):
+        v, it, st = self._outs(sbus)
+        ms = C.c_double(0)
+        check(lib.pf_multi_autotune(self._h, _dptr(sbus), _dptr(v0), float(tol), int(maxit), _dptr(v), _dptr(it),
+                                    _dptr(st), _stream(), C.byref(ms)), "pf_multi_autotune")
+        return {**self.config, "ms": ms.value}
+
+    def set_config(self, warps, blocks_per_sm):
+        check(lib.pf_multi_set_config(self._h, int(warps), int(blocks_per_sm)), "pf_multi_set_config")
+
+    @property
+    def config(self):
+        w, b, n, i = C.c_int(0), C.c_int(0), C.c_int64(0), C.c_int(0)
+        check(lib.pf_multi_get_config(self._h, C.byref(w), C.byref(b), C.byref(n), C.byref(i)), "config")
+        return {"warps": w.value, "blocks_per_sm": b.value, "instances": n.value, "items": i.value}
