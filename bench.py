@@ -170,6 +170,27 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank bookkeeping (weak scaling: every rank solves its own scenarios)
+# ---------------------------------------------------------------------------
+def rank_scenarios(name, g, rank, batch=None):
+    """Scenarios of one rank: the workload's distribution drawn with seed 1 + rank."""
+    return gridgen.config_scenarios(name, g, batch=batch, seed=1 + rank)
+
+
+def combine_ranks(ms, converged, device):
+    """Max elapsed time over ranks and the total converged instances of the
+    job (value = total / max time); a no-op without a process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    c = torch.tensor([float(converged)], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(c)
+    return float(t.item()), float(c.item())
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def dense_update_flop(ndp, kb):
@@ -290,7 +311,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     name = args.config
     g = gridgen.make_grid(name)
-    sc = gridgen.config_scenarios(name, g, batch=args.batch or None, seed=1 + rank)
+    sc = rank_scenarios(name, g, rank, batch=args.batch or None)
     S_np, V0_np = sc.sbus(g), sc.v0_flat(g)
     B = S_np.shape[0]
     S = torch.from_numpy(S_np).to(dev)
@@ -331,17 +352,11 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     prof = plan.profile_read()
     clk = clocks.stop()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
     iters = out[1].cpu().numpy()
     status = out[2].cpu().numpy()
     conv = int(np.sum(status == 0))
-    conv_t = torch.tensor([conv], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(conv_t)
-    value = float(conv_t.item()) * args.steps / (ms_max / 1e3)
+    ms_max, conv_all = combine_ranks(ms, conv, dev)
+    value = conv_all * args.steps / (ms_max / 1e3)
     launches = int(sum(v[0] for v in prof.values()))
 
     # ---- end to end through the public API with host buffers ----
@@ -363,11 +378,8 @@ def run_ours(args):
         st_h.copy_(st, non_blocking=True)
     e1.record(stream)
     barrier()
-    ms_e2e = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_e2e, op=dist.ReduceOp.MAX)
-    conv_e2e = int(np.sum(st_h.numpy() == 0)) * world
-    e2e_value = conv_e2e * args.steps / (float(ms_e2e.item()) / 1e3)
+    ms_e2e, conv_e2e = combine_ranks(e0.elapsed_time(e1), int(np.sum(st_h.numpy() == 0)), dev)
+    e2e_value = conv_e2e * args.steps / (ms_e2e / 1e3)
     h2d = 2 * B * g.n * 16
     d2h = B * g.n * 16 + B * 4 + B
 

@@ -198,6 +198,71 @@ int pf_multi_autotune(pf_multi* mp, const double* sbus, const double* v0, double
 
 void pf_multi_destroy(pf_multi* mp);
 
+/* ---- learned warm start (BF16 tensor-core MLP) ----
+ * The paper motivates fast repeated power flows with the training of neural
+ * networks on many solutions (Sec. 1); here the solver also feeds one: an
+ * MLP maps per-bus injections to an initial voltage guess, and Newton then
+ * runs from that guess to the same tolerance (flat start as fallback).
+ * Network: h1 = GELU(x W1^T + b1), h2 = GELU(h1 W2^T + b2), y = h2 W3^T + b3,
+ * exact erf-GELU, weights [out][in] FP32 master copies, BF16 tensor-core
+ * GEMMs (tcgen05, FP32 accumulate) in the forward and backward passes, loss =
+ * mean squared error on standardised inputs and targets, AdamW (beta 0.9 /
+ * 0.999, eps 1e-8, decoupled weight decay). */
+typedef struct pf_mlp pf_mlp;
+
+/* nh1, nh2 must be multiples of 128; bmax = largest batch of any call.
+ * Weights uniform(+-1/sqrt(fan_in)) from a seeded generator, biases zero. */
+int pf_mlp_create(int nin, int nh1, int nh2, int nout, int bmax, uint64_t seed, pf_mlp** out);
+
+/* host in: per-feature means and standard deviations (nonzero) of the inputs
+ * [nin] and targets [nout] used to standardise them. */
+int pf_mlp_set_norm(pf_mlp* p, const float* mux, const float* sdx, const float* muy, const float* sdy);
+
+/* Standardisation fitted on a training set: per-column mean and standard
+ * deviation of x [B, nin] and t [B, nout] (device, FP32); constant columns
+ * keep scale 1. */
+int pf_mlp_fit_norm(pf_mlp* p, int64_t B, const float* X, const float* T, void* stream);
+
+/* set != 0: load the 6 host arrays W1 [nh1*nin], b1, W2, b2, W3, b3 (and reset
+ * the optimiser); set == 0: copy them out.  Synchronous. */
+int pf_mlp_params(pf_mlp* p, int set, float* const* host);
+
+/* Gradients of the last pf_mlp_train_step, same 6-array layout (host out). */
+int pf_mlp_grads(pf_mlp* p, float* const* host);
+
+/* device in: x [B, nin] FP32 (raw units); device out: y [B, nout] FP32 (raw
+ * units).  Errors: NRPF_ERR_CAPACITY when B > bmax. */
+int pf_mlp_predict(pf_mlp* p, int B, const float* x, float* y, void* stream);
+
+/* One training step on a minibatch: forward, loss, backward, and (update != 0)
+ * an AdamW update with learning rate lr and weight decay wd.
+ * device in: x [B, nin], t [B, nout] FP32 raw units; device out: *loss_out
+ * (FP32, may be NULL) = mean squared standardised error. */
+int pf_mlp_train_step(pf_mlp* p, int B, const float* x, const float* t, float lr, float wd, int update,
+                      float* loss_out, void* stream);
+
+/* 1 if a tensor-core kernel gave up waiting for its MMAs (bounded wait). */
+int pf_mlp_error(pf_mlp* p);
+
+void pf_mlp_destroy(pf_mlp* p);
+
+/* Standalone tensor-core GEMM: C[M,N] FP32 = A[M,K] B[N,K]^T with A, B BF16
+ * row-major on the device; M, N multiples of 128, K of 64.  *err (device int)
+ * is set to 1 on an MMA wait timeout. */
+int pf_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int* err, void* stream);
+
+/* Warm-start glue (device in/out):
+ * features: X [B, 2n] = [P_0..P_{n-1}, Q_0..Q_{n-1}] of sbus [B, n];
+ * targets : T [B, 2 nns] = [|V|, angle] of the nns non-slack buses of V [B, n],
+ *           nsidx [n] = rank of a bus among the non-slack buses, -1 for slack;
+ * v0      : start voltages from a prediction Y [B, 2 nns]: slack buses keep
+ *           v_flat, PV buses keep |v_flat| with the predicted angle, PQ buses
+ *           take the predicted magnitude and angle. */
+int pf_warmstart_features(int n, int B, const double* sbus, float* X, void* stream);
+int pf_warmstart_targets(int n, int B, const int32_t* nsidx, int nns, const double* v, float* T, void* stream);
+int pf_warmstart_v0(int n, int B, const int32_t* nsidx, const int8_t* bus_type, int nns, const float* Y,
+                    const double* v_flat, double* v0, void* stream);
+
 /* ---- launch accounting and per-kernel device time ----
  * Kernel classes (index into the pf_profile arrays): 0 load (input transpose),
  * 1 store, 2 mismatch_jacobian, 3 check, 4 zero_lu, 5 set_ones,

@@ -50,6 +50,9 @@ EXPORTS = ["pf_options_default", "pf_ybus_from_branches", "pf_plan_create", "pf_
            "pf_stage_linear_solve", "pf_profile_start", "pf_profile_read", "pf_kernel_class_name",
            "pf_fma_peak", "pf_stage_mismatch_noalloc", "pf_multi_create", "pf_multi_solve",
            "pf_multi_set_config", "pf_multi_get_config", "pf_multi_autotune", "pf_multi_destroy",
+           "pf_mlp_create", "pf_mlp_set_norm", "pf_mlp_fit_norm", "pf_mlp_params", "pf_mlp_grads",
+           "pf_mlp_predict", "pf_mlp_train_step", "pf_mlp_error", "pf_mlp_destroy", "pf_gemm_bf16",
+           "pf_warmstart_features", "pf_warmstart_targets", "pf_warmstart_v0",
            "pf_plan_destroy", "pf_status_str"]
 
 
@@ -81,6 +84,20 @@ def _load():
     lib.pf_multi_autotune.argtypes = [P, P, P, D, I, P, P, P, P, C.POINTER(D)]
     lib.pf_multi_destroy.argtypes = [P]
     lib.pf_multi_destroy.restype = None
+    lib.pf_mlp_create.argtypes = [I, I, I, I, I, C.c_uint64, C.POINTER(C.c_void_p)]
+    lib.pf_mlp_set_norm.argtypes = [P, P, P, P, P]
+    lib.pf_mlp_fit_norm.argtypes = [P, I64, P, P, P]
+    lib.pf_mlp_params.argtypes = [P, I, P]
+    lib.pf_mlp_grads.argtypes = [P, P]
+    lib.pf_mlp_predict.argtypes = [P, I, P, P, P]
+    lib.pf_mlp_train_step.argtypes = [P, I, P, P, C.c_float, C.c_float, I, P, P]
+    lib.pf_mlp_error.argtypes = [P]
+    lib.pf_mlp_destroy.argtypes = [P]
+    lib.pf_mlp_destroy.restype = None
+    lib.pf_gemm_bf16.argtypes = [P, P, P, I, I, I, P, P]
+    lib.pf_warmstart_features.argtypes = [I, I, P, P, P]
+    lib.pf_warmstart_targets.argtypes = [I, I, P, I, P, P, P]
+    lib.pf_warmstart_v0.argtypes = [I, I, P, P, I, P, P, P, P]
     lib.pf_plan_destroy.argtypes = [P]
     lib.pf_plan_destroy.restype = None
     lib.pf_status_str.argtypes = [I]
