@@ -56,7 +56,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="mesh2000_b10k", choices=list(gridgen.CONFIGS) + ["feeders256x100"])
+    ap.add_argument("--config", default="mesh2000_b10k",
+                    choices=list(gridgen.CONFIGS) + ["feeders256x100", "warmstart2000"])
+    ap.add_argument("--train-samples", type=int, default=200000)
+    ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=0, help="override the batch size (0 = the workload's)")
     ap.add_argument("--lu", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--maxit", type=int, default=MAXIT)
@@ -294,6 +297,115 @@ def run_feeders(args):
     mp.close()
 
 
+def run_warmstart(args):
+    """Learned warm start on the 2,000-bus grid: 200,000 solver-made solutions
+    (scenario seeds 2, 3, ...) train the 4000-1024-1024-3998 network; the
+    10,000 held-out scenarios (seed 1, the 2,000-bus workload) are then solved
+    from its guesses and from flat start, NR to 1e-8 p.u. with fallback."""
+    import torch
+
+    import paper_2101_02270_gb300 as pf
+    from paper_2101_02270_gb300 import warmstart as wsm
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    g = gridgen.make_grid("mesh2000_b10k")
+    plan64 = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, max_batch=10000)
+    plan32 = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision="fp32", max_batch=10000)
+    nns = int(np.sum(g.bus_type != 3))
+    net = wsm.MLP(2 * g.n, 1024, 1024, 2 * nns, bmax=1024, seed=0)
+    ws64 = wsm.WarmStart(plan64, g.bus_type, net)
+    ws32 = wsm.WarmStart(plan32, g.bus_type, net)
+    # ---- training data from the solver itself ----
+    t0 = time.perf_counter()
+    chunk = 10000
+    nchunks = max(1, args.train_samples // chunk)
+    Xs, Ts = [], []
+    for c in range(nchunks):
+        sc = gridgen.config_scenarios("mesh2000_b10k", g, batch=chunk, seed=2 + c)
+        S = torch.from_numpy(sc.sbus(g)).to(dev)
+        V, it, st = plan32.solve(S, torch.from_numpy(sc.v0_flat(g)).to(dev), TOL, 20)
+        ok = st == 0
+        Xs.append(ws32.features(S)[ok])
+        Ts.append(ws32.targets(V)[ok])
+    X = torch.cat(Xs)
+    T = torch.cat(Ts)
+    del Xs, Ts
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    # ---- training ----
+    net.fit_norm(X, T)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    loss = None
+    t0 = time.perf_counter()
+    steps = args.train_steps
+    for step in range(steps):
+        lr = 1e-3 * (0.5 * (1 + np.cos(np.pi * step / steps))) + 2e-5
+        idx = torch.randint(0, X.shape[0], (1024,), device=dev, generator=gen)
+        loss = net.train_step(X[idx].contiguous(), T[idx].contiguous(), lr=lr, wd=1e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    final_loss = float(loss.item())
+    del X, T
+    # ---- held-out evaluation ----
+    ho = gridgen.config_scenarios("mesh2000_b10k", g, seed=1)
+    S_np, V0_np = ho.sbus(g), ho.v0_flat(g)
+    Sh = torch.from_numpy(S_np).to(dev)
+    Vh = torch.from_numpy(V0_np).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, r
+
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    ms_flat64, (vf, itf, stf) = timed(lambda: plan64.solve(Sh, Vh, TOL, MAXIT))
+    ms_warm64, (vw, itw, stw, fb) = timed(lambda: ws64.solve(Sh, Vh, TOL, MAXIT))
+    ms_flat32, (vf32, itf32, stf32) = timed(lambda: plan32.solve(Sh, Vh, TOL, 20))
+    ms_warm32, (vw32, itw32, stw32, fb32) = timed(lambda: ws32.solve(Sh, Vh, TOL, 20))
+    clk = clocks.stop()
+    B = S_np.shape[0]
+    conv = int((stw == 0).sum().item())
+    value = conv / (ms_warm64 / 1e3)
+    dv = float((vw - vf).abs().max().item())
+    # oracle check of a sample of warm-started results
+    from oracle import nrpf
+    Y = nrpf.make_ybus(g.n, g.f, g.t, g.r, g.x, g.b)
+    idx = np.random.default_rng(0).choice(B, 8, replace=False)
+    Vo, ito, sto = nrpf.newton_batch(Y, S_np[idx], V0_np[idx], g.bus_type, TOL, MAXIT)
+    vw_np = vw.cpu().numpy()
+    d_or = float(np.max(np.abs(vw_np[idx] - Vo)))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_warm64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 (NR) + bf16 (MLP)", "data": "synthetic",
+        "config": {"workload": "warmstart2000", "buses": g.n, "held_out": B, "train_samples": nchunks * chunk,
+                   "train_steps": steps, "mlp": [2 * g.n, 1024, 1024, 2 * nns], "tol": TOL},
+        "warm_fp64": {"flows_s": value, "ms": ms_warm64, "iters_mean": float(itw.float().mean()),
+                      "fallbacks": int(fb.sum()), "converged": conv},
+        "flat_fp64": {"flows_s": int((stf == 0).sum()) / (ms_flat64 / 1e3), "ms": ms_flat64,
+                      "iters_mean": float(itf.float().mean())},
+        "warm_fp32lu": {"flows_s": int((stw32 == 0).sum()) / (ms_warm32 / 1e3), "ms": ms_warm32,
+                        "iters_mean": float(itw32.float().mean()), "fallbacks": int(fb32.sum())},
+        "flat_fp32lu": {"flows_s": int((stf32 == 0).sum()) / (ms_flat32 / 1e3), "ms": ms_flat32,
+                        "iters_mean": float(itf32.float().mean())},
+        "max_dv_warm_vs_flat": dv, "max_dv_warm_vs_oracle_sample": d_or,
+        "training": {"generate_s": round(gen_s, 2), "train_s": round(train_s, 2), "final_loss": final_loss},
+        "clocks": clk, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -447,6 +559,8 @@ def main():
         run_reference(args)
     elif args.config == "feeders256x100":
         run_feeders(args)
+    elif args.config == "warmstart2000":
+        run_warmstart(args)
     else:
         run_ours(args)
 

@@ -232,13 +232,20 @@ __global__ void k_zero16(uint4* __restrict__ p, size_t n16, const int32_t* __res
     p[i] = z;
 }
 
-// Identity on the padding of the dense block.
+// Identity on the padding of the dense block, and zero right-hand side on
+// its padding rows (m .. s+ndp-1): no other kernel writes those rows, and a
+// stale non-finite value there would leak into real rows as 0 * NaN during
+// the backward substitution.
 template <typename T>
 __global__ void k_set_ones(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;
   const int tile = blockIdx.y, lane = threadIdx.x;
   T* LU = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;
-  for (int t = threadIdx.y; t < P.n_one; t += blockDim.y) LU[(size_t)P.one_pos[t] * kTile + lane] = (T)1;
+  T* X = reinterpret_cast<T*>(S.x) + (size_t)tile * P.mp * kTile;
+  for (int t = threadIdx.y; t < P.n_one; t += blockDim.y) {
+    LU[(size_t)P.one_pos[t] * kTile + lane] = (T)1;
+    X[(size_t)(P.m + t) * kTile + lane] = (T)0;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -301,7 +308,7 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
 //   (a) k_dense_diag   : factor the kb x kb diagonal block, store 1/pivots
 //   (b) k_dense_panel  : L21 = A21 U11^-1 (rows) and U12 = L11^-1 A12 (cols),
 //                        four rows or four columns per thread
-//   (c) k_dense_update : A22 -= L21 U12, a 4 x 4 register tile per thread
+//   (c) k_dense_update : A22 -= L21 U12, a register tile per thread (4x4 FP64, 8x8 FP32)
 // ---------------------------------------------------------------------------
 template <typename T, int KB>
 __global__ void k_dense_diag(DevPlan P, DevState S, int k, const int32_t* __restrict__ gate) {
@@ -396,7 +403,7 @@ __global__ void k_dense_panel(DevPlan P, DevState S, int k, const int32_t* __res
   }
 }
 
-template <typename T, int KB>
+template <typename T, int KB, int TS>
 __global__ void k_dense_update(DevPlan P, DevState S, int k, const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;
   const int lane = threadIdx.x;
@@ -404,34 +411,40 @@ __global__ void k_dense_update(DevPlan P, DevState S, int k, const int32_t* __re
   if (!tile_active(S, tile, lane)) return;
   const int ld = P.ndp;
   const int r0 = k + KB;
-  const int nb = (ld - r0) / 4;
+  const int nb = (ld - r0) / TS;
   const int t = blockIdx.x * blockDim.y + threadIdx.y;
   if (t >= nb * nb) return;
   const int bi = t % nb, bj = t / nb;
-  const int i0 = r0 + 4 * bi, j0 = r0 + 4 * bj;
+  const int i0 = r0 + TS * bi, j0 = r0 + TS * bj;
   T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
-  auto at = [&](int r, int c) -> T& { return A[((size_t)c * ld + r) * kTile]; };
-  T acc[4][4];
+  // element (r, c) of the block is A[(c * ld + r) * 32]; rows of one column
+  // are 32 elements apart, so every access below is a column pointer plus a
+  // compile-time offset
+  const size_t cstride = (size_t)ld * kTile;
+  T* __restrict__ cj = A + (size_t)j0 * cstride + (size_t)i0 * kTile;  // (i0, j0)
+  const T* __restrict__ pa = A + (size_t)k * cstride + (size_t)i0 * kTile;  // (i0, k)
+  const T* __restrict__ pb = A + (size_t)j0 * cstride + (size_t)k * kTile;  // (k, j0)
+  T acc[TS][TS];
 #pragma unroll
-  for (int c = 0; c < 4; ++c)
+  for (int c = 0; c < TS; ++c)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) acc[r][c] = at(i0 + r, j0 + c);
+    for (int r = 0; r < TS; ++r) acc[r][c] = cj[c * cstride + r * kTile];
 #pragma unroll
   for (int p = 0; p < KB; ++p) {
-    T a[4], b[4];
+    T a[TS], b[TS];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) a[r] = at(i0 + r, k + p);
+    for (int r = 0; r < TS; ++r) a[r] = pa[p * cstride + r * kTile];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) b[c] = at(k + p, j0 + c);
+    for (int c = 0; c < TS; ++c) b[c] = pb[c * cstride + p * kTile];
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+    for (int c = 0; c < TS; ++c)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[r][c] -= a[r] * b[c];
+      for (int r = 0; r < TS; ++r) acc[r][c] -= a[r] * b[c];
   }
 #pragma unroll
-  for (int c = 0; c < 4; ++c)
+  for (int c = 0; c < TS; ++c)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) at(i0 + r, j0 + c) = acc[r][c];
+    for (int r = 0; r < TS; ++r) cj[c * cstride + r * kTile] = acc[r][c];
 }
 
 // ---------------------------------------------------------------------------
@@ -473,41 +486,18 @@ __global__ void k_bwd_level(DevPlan P, DevState S, int r0, int r1, const int32_t
   X[(size_t)i * kTile] = acc / LU[(size_t)P.dp[i] * kTile];
 }
 
-// Dense block solves, one lane per instance: unit-lower forward, then upper
-// backward substitution on rows s .. s+ndp-1 of the right-hand side.
-template <typename T>
-__global__ void k_dense_solve(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
-  if (gate && *gate == 0) return;
-  const int lane = threadIdx.x;
-  const int tile = blockIdx.x * blockDim.y + threadIdx.y;
-  if (tile * kTile >= S.Bp) return;
-  if (!tile_active(S, tile, lane)) return;
-  const T* __restrict__ A = reinterpret_cast<const T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
-  T* __restrict__ X = reinterpret_cast<T*>(S.x) + ((size_t)tile * P.mp + P.s) * kTile + lane;
-  const int ld = P.ndp;
-  for (int c = 0; c < ld; ++c) {  // column-oriented forward: x[r] -= L[r][c] x[c]
-    const T xc = X[(size_t)c * kTile];
-    for (int r = c + 1; r < ld; ++r) X[(size_t)r * kTile] -= A[((size_t)c * ld + r) * kTile] * xc;
-  }
-  for (int c = ld - 1; c >= 0; --c) {  // column-oriented backward
-    const T xc = X[(size_t)c * kTile] / A[((size_t)c * ld + c) * kTile];
-    X[(size_t)c * kTile] = xc;
-    for (int r = 0; r < c; ++r) X[(size_t)r * kTile] -= A[((size_t)c * ld + r) * kTile] * xc;
-  }
-}
 
 // Dense block solves with one tile's right-hand side held in shared memory.
 // CTA = one tile (32 instances) x kSolveWarps warps.  Forward (unit lower) and
 // backward (upper) substitution by blocks of SB columns: warp 0 solves the
 // SB x SB diagonal block, then every warp updates its share of the remaining
 // rows with SB multiply-adds each (the row updates of a block are independent).
-constexpr int kSolveWarps = 4;
+constexpr int kSolveWarps = 8;
 
-template <typename T, int SB>
+template <typename T, int SB, bool SMEM>
 __global__ void __launch_bounds__(32 * kSolveWarps) k_dense_solve_smem(DevPlan P, DevState S,
                                                                        const int32_t* __restrict__ gate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xs = reinterpret_cast<T*>(smem_raw);  // [ndp][32]
   if (gate && *gate == 0) return;
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int tile = blockIdx.x;
@@ -515,8 +505,13 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_dense_solve_smem(DevPlan P
   const T* __restrict__ A = reinterpret_cast<const T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
   T* __restrict__ X = reinterpret_cast<T*>(S.x) + ((size_t)tile * P.mp + P.s) * kTile + lane;
   const int ld = P.ndp;
-  for (int r = warp; r < ld; r += kSolveWarps) xs[r * kTile + lane] = X[(size_t)r * kTile];
-  __syncthreads();
+  // the tile's right-hand side: in shared memory when it fits, else in place
+  // in global memory (same blocked algorithm, L2-resident per tile)
+  T* xs = SMEM ? reinterpret_cast<T*>(smem_raw) : X - lane;  // xs[r * 32 + lane]
+  if (SMEM) {
+    for (int r = warp; r < ld; r += kSolveWarps) xs[r * kTile + lane] = X[(size_t)r * kTile];
+    __syncthreads();
+  }
   for (int k0 = 0; k0 < ld; k0 += SB) {
     if (warp == 0) {
 #pragma unroll
@@ -561,7 +556,8 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_dense_solve_smem(DevPlan P
     }
     __syncthreads();
   }
-  for (int r = warp; r < ld; r += kSolveWarps) X[(size_t)r * kTile] = xs[r * kTile + lane];
+  if (SMEM)
+    for (int r = warp; r < ld; r += kSolveWarps) X[(size_t)r * kTile] = xs[r * kTile + lane];
 }
 
 // ---------------------------------------------------------------------------
@@ -713,8 +709,11 @@ static void launch_dense_step(const DevPlan& P, const DevState& S, int k, const 
   if (rem > 0) {
     NRPF_LAUNCH(rec, K_DENSE_PANEL, st,
                 k_dense_panel<T, KB><<<grid2(2 * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate));
+    // register tile: 4 x 4 for FP64 (the FP64 pipe is the bound), 8 x 8 for
+    // FP32 (halves the loads per multiply-add; FP32 is load-bound)
+    constexpr int TS = (sizeof(T) == 4 && KB >= 8) ? 8 : 4;
     NRPF_LAUNCH(rec, K_DENSE_UPDATE, st,
-                k_dense_update<T, KB><<<grid2((int64_t)(rem / 4) * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(
+                k_dense_update<T, KB, TS><<<grid2((int64_t)(rem / TS) * (rem / TS), 4, tiles), dim3(32, 4), 0, st>>>(
                     P, S, k, gate));
   }
 }
@@ -747,12 +746,16 @@ static void launch_dense_solve_smem(const DevPlan& P, const DevState& S, const i
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !configured[dev]) {
-    cudaFuncSetAttribute(k_dense_solve_smem<T, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_dense_solve_smem<T, SB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kSolveSmemMax);
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  NRPF_LAUNCH(rec, K_DENSE_SOLVE, st,
-              k_dense_solve_smem<T, SB><<<S.Bp / kTile, dim3(32, kSolveWarps), smem, st>>>(P, S, gate));
+  if (smem <= kSolveSmemMax)
+    NRPF_LAUNCH(rec, K_DENSE_SOLVE, st,
+                k_dense_solve_smem<T, SB, true><<<S.Bp / kTile, dim3(32, kSolveWarps), smem, st>>>(P, S, gate));
+  else
+    NRPF_LAUNCH(rec, K_DENSE_SOLVE, st,
+                k_dense_solve_smem<T, SB, false><<<S.Bp / kTile, dim3(32, kSolveWarps), 0, st>>>(P, S, gate));
 }
 
 template <typename T>
@@ -767,15 +770,10 @@ void launch_solve(const DevPlan& P, const DevState& S, const std::vector<int32_t
   }
   if (P.ndp > 0) {
     const size_t smem = (size_t)P.ndp * kTile * sizeof(T);
-    if (smem <= kSolveSmemMax) {
-      if (P.ndp % 8 == 0)
-        launch_dense_solve_smem<T, 8>(P, S, gate, st, rec, smem);
-      else
-        launch_dense_solve_smem<T, 4>(P, S, gate, st, rec, smem);
-    } else {
-      NRPF_LAUNCH(rec, K_DENSE_SOLVE, st,
-                  k_dense_solve<T><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, gate));
-    }
+    if (P.ndp % 8 == 0)
+      launch_dense_solve_smem<T, 8>(P, S, gate, st, rec, smem);
+    else
+      launch_dense_solve_smem<T, 4>(P, S, gate, st, rec, smem);
   }
   for (size_t l = 0; l + 1 < bw_lvl.size(); ++l) {
     int r0 = bw_lvl[l], r1 = bw_lvl[l + 1];

@@ -216,3 +216,19 @@ def test_mixed_precision_lu(name, B):
     Vo, ito, sto = _oracle_solve(g, S, V0, idx=idx)
     _compare_newton(g, Vg[idx], itg[idx], stg[idx], Vo, ito, sto, S[idx], check_iters=False)
     assert np.all(itg[idx] >= ito) and np.all(itg[idx] <= ito + 3)
+
+
+def test_fresh_workspace_ignores_stale_memory():
+    """A plan whose workspace reuses memory freed by another plan (here full of
+    NaN from a failed instance) still gives clean results: nothing of the
+    solve reads workspace it did not write first."""
+    g, S, V0 = case("mesh30_b64", batch=32)
+    Sb = S.copy()
+    Sb[:, 4] = np.nan
+    with _plan(g) as p:
+        p.solve(_dev(Sb), _dev(V0), TOL, 10)
+        torch.cuda.synchronize()
+    for _ in range(3):
+        with _plan(g) as p:
+            v, it, st = p.solve(_dev(S), _dev(V0), TOL, 10)
+            assert np.all(st.cpu().numpy() == 0)
