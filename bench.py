@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--dense-frac", type=float, default=0.7)
     ap.add_argument("--panel", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-all", action="store_true",
+                    help="diagnostic: CUDA-event timing of every kernel class (adds two events per launch)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -143,30 +145,48 @@ def oracle_sample(g, S, V0, seconds, cores):
 
 
 def run_reference(args):
+    """The CPU FP64 oracle on the host cores, on the same workload and metric
+    (each step a bounded sample of the workload)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     name = args.config
-    g = gridgen.make_grid(name)
-    sc = gridgen.config_scenarios(name, g, batch=args.batch or None)
-    S, V0 = sc.sbus(g), sc.v0_flat(g)
+    if name == "feeders256x100":
+        fs = gridgen.make_feeders()
+        scen = gridgen.grids.feeder_scenarios(fs)
+        # a sample mixing feeders: every 16th feeder, its scenarios
+        cases = [(fs[i], scen[i].sbus(fs[i]), scen[i].v0_flat(fs[i])) for i in range(0, len(fs), 16)]
+        batch = sum(sc.batch for sc in scen)
+    else:
+        gname = "mesh2000_b10k" if name == "warmstart2000" else name
+        g = gridgen.make_grid(gname)
+        sc = gridgen.config_scenarios(gname, g, batch=args.batch or None)
+        cases = [(g, sc.sbus(g), sc.v0_flat(g))]
+        batch = int(sc.batch)
     cores = os.cpu_count() or 1
     per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+
+    def one(seconds):
+        vals, last = [], None
+        for g, S, V0 in cases:
+            last = oracle_sample(g, S, V0, seconds / len(cases), cores)
+            vals.append(last["value"])
+        return statistics.mean(vals), last
+
     for _ in range(args.warmup):
-        oracle_sample(g, S, V0, min(per_step, 2.0), cores)
+        one(min(per_step, 2.0))
     vals = []
     last = None
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        last = oracle_sample(g, S, V0, per_step, cores)
-        vals.append(last["value"])
+        v, last = one(per_step)
+        vals.append(v)
     dt = time.perf_counter() - t0
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": name, "batch": int(S.shape[0]), "tol": TOL,
-                                            "maxit": MAXIT},
+            "data": "synthetic", "config": {"workload": name, "batch": batch, "tol": TOL, "maxit": MAXIT},
             "cpu_baseline": dict(last, value=value),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -406,6 +426,79 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+def run_small(args):
+    """30-bus meshed grid, 64 scenarios: a latency case.  Solved by the fused
+    persistent kernel (pf_multi_*, one graph launch, pure sparse plan) and,
+    for comparison, by the multi-kernel pf_solve_batch path."""
+    import torch
+
+    import paper_2101_02270_gb300 as pf
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    name = args.config
+    g = gridgen.make_grid(name)
+    sc = gridgen.config_scenarios(name, g, batch=args.batch or None)
+    S_np, V0_np = sc.sbus(g), sc.v0_flat(g)
+    B = S_np.shape[0]
+    plan = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision=args.lu, dense_frac=1.0)
+    mp = pf.MultiPlan([plan], [B])
+    Sd = torch.from_numpy(S_np.ravel()).to(dev)
+    Vd = torch.from_numpy(V0_np.ravel()).to(dev)
+    tuned = mp.autotune(Sd, Vd, TOL, args.maxit)
+    out = mp._outs(Sd)
+    stream = torch.cuda.current_stream()
+    plan_mk = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision=args.lu)
+    S2 = torch.from_numpy(S_np).to(dev)
+    V2 = torch.from_numpy(V0_np).to(dev)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(lambda: mp.solve(Sd, Vd, TOL, args.maxit, out=out))
+    ms_mk = timed(lambda: plan_mk.solve(S2, V2, TOL, args.maxit))
+    clk = clocks.stop()
+    it = out[1].cpu().numpy()
+    st = out[2].cpu().numpy()
+    conv = int(np.sum(st == 0))
+    # end to end from pinned host memory through the fused path
+    S_h, V_h = torch.from_numpy(S_np.ravel()).pin_memory(), torch.from_numpy(V0_np.ravel()).pin_memory()
+    Vo = torch.empty_like(S_h).pin_memory()
+    Sx, Vx = torch.empty_like(Sd), torch.empty_like(Vd)
+
+    def e2e():
+        Sx.copy_(S_h, non_blocking=True)
+        Vx.copy_(V_h, non_blocking=True)
+        v, i2, s2 = mp.solve(Sx, Vx, TOL, args.maxit, out=out)
+        Vo.copy_(v, non_blocking=True)
+    ms_e2e = timed(e2e)
+    line = {
+        "metric": METRIC, "value": conv / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.lu == "fp64" else "f64+f32lu", "data": "synthetic",
+        "config": {"workload": name, "batch": B, "buses": g.n, "lu_precision": args.lu, "tol": TOL,
+                   "maxit": args.maxit, "path": "fused persistent kernel, CUDA graph", "autotuned": tuned},
+        "latency_us": 1e3 * ms, "multi_kernel_path_ms": ms_mk,
+        "iterations": {"mean": float(it.mean()), "hist": np.bincount(it).tolist()}, "converged": conv,
+        "clocks": clk, "e2e": {"value": conv / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(2 * S_h.nbytes),
+                               "d2h_bytes_per_step": int(S_h.nbytes)},
+        "gpu_launches": 1,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -453,7 +546,8 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    plan.profile_start(["dense_update"])
+    from paper_2101_02270_gb300.solver import KERNEL_CLASSES
+    plan.profile_start(KERNEL_CLASSES if args.time_all else ["dense_update"])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
@@ -561,6 +655,8 @@ def main():
         run_feeders(args)
     elif args.config == "warmstart2000":
         run_warmstart(args)
+    elif args.config == "mesh30_b64":
+        run_small(args)
     else:
         run_ours(args)
 
