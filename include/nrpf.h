@@ -247,9 +247,16 @@ int pf_mlp_error(pf_mlp* p);
 void pf_mlp_destroy(pf_mlp* p);
 
 /* Standalone tensor-core GEMM: C[M,N] FP32 = A[M,K] B[N,K]^T with A, B BF16
- * row-major on the device; M, N multiples of 128, K of 64.  *err (device int)
- * is set to 1 on an MMA wait timeout. */
-int pf_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int* err, void* stream);
+ * row-major on the device; M, N multiples of 128, K of 64.  variant 0: tiles
+ * copied by the CTA then multiplied (one stage); variant 1: TMA-filled
+ * four-stage ring with a producer thread and an MMA-issuing thread.
+ * *err (device int) is set to 1 when a kernel gives up a bounded wait. */
+int pf_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int variant, int* err,
+                 void* stream);
+
+/* GEMM variant used by the network (default 1; 0 when the TMA encoder is
+ * unavailable). */
+int pf_gemm_set_variant(int variant);
 
 /* Warm-start glue (device in/out):
  * features: X [B, 2n] = [P_0..P_{n-1}, Q_0..Q_{n-1}] of sbus [B, n];

@@ -52,6 +52,7 @@ EXPORTS = ["pf_options_default", "pf_ybus_from_branches", "pf_plan_create", "pf_
            "pf_multi_set_config", "pf_multi_get_config", "pf_multi_autotune", "pf_multi_destroy",
            "pf_mlp_create", "pf_mlp_set_norm", "pf_mlp_fit_norm", "pf_mlp_params", "pf_mlp_grads",
            "pf_mlp_predict", "pf_mlp_train_step", "pf_mlp_error", "pf_mlp_destroy", "pf_gemm_bf16",
+           "pf_gemm_set_variant",
            "pf_warmstart_features", "pf_warmstart_targets", "pf_warmstart_v0",
            "pf_plan_destroy", "pf_status_str"]
 
@@ -94,7 +95,8 @@ def _load():
     lib.pf_mlp_error.argtypes = [P]
     lib.pf_mlp_destroy.argtypes = [P]
     lib.pf_mlp_destroy.restype = None
-    lib.pf_gemm_bf16.argtypes = [P, P, P, I, I, I, P, P]
+    lib.pf_gemm_bf16.argtypes = [P, P, P, I, I, I, I, P, P]
+    lib.pf_gemm_set_variant.argtypes = [I]
     lib.pf_warmstart_features.argtypes = [I, I, P, P, P]
     lib.pf_warmstart_targets.argtypes = [I, I, P, I, P, P, P]
     lib.pf_warmstart_v0.argtypes = [I, I, P, P, I, P, P, P, P]

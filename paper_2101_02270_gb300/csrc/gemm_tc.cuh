@@ -203,3 +203,138 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const __nv_bfloat16* _
 constexpr size_t kGemmSmem = 64 * 1024;
 
 }  // namespace nrpf
+
+// ---------------------------------------------------------------------------
+// Pipelined variant: TMA (cp.async.bulk.tensor) fills a ring of kStages
+// shared-memory stages with 128-byte-swizzled tiles; thread 0 of warp 0
+// produces (expect-tx + two TMA loads per stage), thread 0 of warp 1 issues
+// the MMAs of each stage as soon as its bytes have landed and commits them to
+// the stage's "empty" barrier, which releases the stage to the producer.  The
+// accumulator is complete when a final commit arrives on "done"; then all four
+// warps run the same epilogue as k_gemm_tc.  Every wait is bounded.
+// ---------------------------------------------------------------------------
+namespace nrpf {
+
+constexpr int kStages = 4;
+constexpr uint32_t kStageBytes = (kGemmBM + kGemmBN) * kGemmBK * 2;  // 32 KB
+constexpr size_t kGemmTmaSmem = (size_t)kStages * kStageBytes + 1024;
+
+// Shared-memory descriptor, K-major with 128-byte swizzle: 8-row atoms of
+// 1024 B (stride byte offset), leading byte offset unused (1), layout type 2.
+__device__ __forceinline__ uint64_t make_sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// bounded wait; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t spins = 0; spins < kMbarSpinLimit; ++spins)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+template <class Epi, class TMap>
+__global__ void __launch_bounds__(kGemmThreads) k_gemm_tma(const __grid_constant__ TMap tmA,
+                                                           const __grid_constant__ TMap tmB, int M, int N, int K,
+                                                           Epi epi, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte alignment for the swizzled tiles
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kGemmBM, n0 = blockIdx.x * kGemmBN;
+  const int nk = K / kGemmBK;
+  if (warp == 0) tmem_alloc(&tmem_holder, kTmemCols);
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_holder;
+  const uint32_t base = smem_u32(smem);
+  if (warp == 0 && lane == 0) {
+    // producer
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % kStages;
+      if (kc >= kStages && !mbar_wait(&empty[s], ((kc / kStages) - 1) & 1)) {
+        s_fail = 1;
+        break;
+      }
+      const uint32_t sa = base + s * kStageBytes, sb = sa + kGemmBM * kGemmBK * 2;
+      mbar_expect_tx(&full[s], kStageBytes);
+      tma_load_2d(sa, &tmA, kc * kGemmBK, m0, &full[s]);
+      tma_load_2d(sb, &tmB, kc * kGemmBK, n0, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = make_idesc_bf16(kGemmBM, kGemmBN);
+    bool ok = true;
+    for (int kc = 0; kc < nk; ++kc) {
+      const int s = kc % kStages;
+      if (!mbar_wait(&full[s], (kc / kStages) & 1)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = base + s * kStageBytes, sb = sa + kGemmBM * kGemmBK * 2;
+#pragma unroll
+      for (int kk = 0; kk < kGemmBK / 16; ++kk)
+        umma_bf16(tmem, make_sdesc_sw128(sa + kk * 32), make_sdesc_sw128(sb + kk * 32), idesc,
+                  (kc > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(&empty[s]);
+    }
+    if (!ok) s_fail = 1;
+    umma_commit(&done);  // arrives once every MMA issued above has completed
+  }
+  const bool got = mbar_wait(&done, 0);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  const bool fail = !got || s_fail;
+  if (fail) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kGemmBN; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) epi(row, n0 + c0 + j, v[j]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+}  // namespace nrpf

@@ -15,6 +15,7 @@
 #include <random>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -58,17 +59,66 @@ struct EpiBias {  // Y = acc + b
   }
 };
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2-D map of a row-major BF16 matrix [rows][K]: boxes of 64 (K) x 128 rows,
+// 128-byte swizzle (the layout the UMMA descriptors expect)
+bool make_tmap(CUtensorMap* m, const bf16* ptr, int rows, int K) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kGemmBK, (cuuint32_t)kGemmBM};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// variant: 0 = copy-then-MMA kernel, 1 = TMA pipeline (falls back to 0 when
+// the tensor-map encoder is unavailable)
+int g_gemm_variant = 1;
+
 template <class Epi>
-int gemm(const bf16* A, const bf16* B, int M, int N, int K, Epi epi, int* err, cudaStream_t st) {
+int gemm(const bf16* A, const bf16* B, int M, int N, int K, Epi epi, int* err, cudaStream_t st,
+         int variant = -1) {
   if (M % kGemmBM || N % kGemmBN || K % kGemmBK || M <= 0 || N <= 0 || K <= 0) return NRPF_ERR_ARG;
+  if (variant < 0) variant = g_gemm_variant;
   static bool configured[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !configured[dev]) {
     cudaFuncSetAttribute(k_gemm_tc<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+    cudaFuncSetAttribute(k_gemm_tma<Epi, CUtensorMap>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kGemmTmaSmem);
     if (dev >= 0 && dev < 64) configured[dev] = true;
   }
-  k_gemm_tc<Epi><<<dim3(N / kGemmBN, M / kGemmBM), kGemmThreads, kGemmSmem, st>>>(A, B, M, N, K, epi, err);
+  CUtensorMap ta, tb;
+  if (variant == 1 && make_tmap(&ta, A, M, K) && make_tmap(&tb, B, N, K)) {
+    k_gemm_tma<Epi, CUtensorMap><<<dim3(N / kGemmBN, M / kGemmBM), kGemmThreads, kGemmTmaSmem, st>>>(ta, tb, M, N, K,
+                                                                                                     epi, err);
+  } else {
+    k_gemm_tc<Epi><<<dim3(N / kGemmBN, M / kGemmBM), kGemmThreads, kGemmSmem, st>>>(A, B, M, N, K, epi, err);
+  }
   return cudaGetLastError() == cudaSuccess ? NRPF_OK : NRPF_ERR_CUDA;
 }
 
@@ -559,10 +609,17 @@ int pf_warmstart_v0(int n, int B, const int32_t* nsidx, const int8_t* bus_type, 
 }
 
 // Standalone tensor-core GEMM: C[M,N] (FP32) = A[M,K] B[N,K]^T (BF16, row-major).
-int pf_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int* err, void* stream) {
-  if (!A || !B || !C || !err) return NRPF_ERR_ARG;
+int pf_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, int variant, int* err,
+                 void* stream) {
+  if (!A || !B || !C || !err || variant < 0 || variant > 1) return NRPF_ERR_ARG;
   return nrpf::gemm(reinterpret_cast<const bf16*>(A), reinterpret_cast<const bf16*>(B), M, N, K, nrpf::EpiF32{C, N},
-                    err, reinterpret_cast<cudaStream_t>(stream));
+                    err, reinterpret_cast<cudaStream_t>(stream), variant);
+}
+
+int pf_gemm_set_variant(int variant) {
+  if (variant < 0 || variant > 1) return NRPF_ERR_ARG;
+  nrpf::g_gemm_variant = variant;
+  return NRPF_OK;
 }
 
 }  // extern "C"

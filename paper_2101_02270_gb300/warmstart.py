@@ -81,13 +81,15 @@ class MLP:
         return lib.pf_mlp_error(self._h)
 
 
-def gemm_bf16(A, B):
-    """C = A B^T on the tensor cores (A [M,K], B [N,K] bfloat16 CUDA tensors)."""
+def gemm_bf16(A, B, variant=1):
+    """C = A B^T on the tensor cores (A [M,K], B [N,K] bfloat16 CUDA tensors).
+    variant 0: one-stage kernel; 1: TMA-pipelined kernel."""
     M, K = A.shape
     N = B.shape[0]
     Cm = torch.empty((M, N), dtype=torch.float32, device=A.device)
     err = torch.zeros(1, dtype=torch.int32, device=A.device)
-    check(lib.pf_gemm_bf16(_dptr(A), _dptr(B), _dptr(Cm), M, N, K, _dptr(err), _stream()), "pf_gemm_bf16")
+    check(lib.pf_gemm_bf16(_dptr(A), _dptr(B), _dptr(Cm), M, N, K, int(variant), _dptr(err), _stream()),
+          "pf_gemm_bf16")
     return Cm, err
 
 

@@ -20,13 +20,15 @@ def _ws():
     return ws
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 192), (512, 1024, 4096), (1024, 256, 1024)])
-def test_tc_gemm_matches_fp32_reference(M, N, K):
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 192), (512, 1024, 4096), (1024, 256, 1024),
+                                   (128, 256, 320)])
+def test_tc_gemm_matches_fp32_reference(M, N, K, variant):
     ws = _ws()
     g = torch.Generator(device="cuda").manual_seed(M + N + K)
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
-    C, err = ws.gemm_bf16(A, B)
+    C, err = ws.gemm_bf16(A, B, variant)
     torch.cuda.synchronize()
     assert err.item() == 0
     ref = A.float() @ B.float().T
