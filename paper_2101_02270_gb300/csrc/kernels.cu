@@ -403,8 +403,16 @@ __global__ void k_dense_panel(DevPlan P, DevState S, int k, const int32_t* __res
   }
 }
 
+// occupancy hint: 128-thread CTAs, at least kUpdMinBlocks resident per SM
+// (the 8x8 FP32 tile is latency-bound when registers limit residency)
+template <typename T, int TS>
+struct UpdOcc {
+  static constexpr int value = (sizeof(T) == 4 && TS == 8) ? 3 : 6;
+};
+
 template <typename T, int KB, int TS>
-__global__ void k_dense_update(DevPlan P, DevState S, int k, const int32_t* __restrict__ gate) {
+__global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevPlan P, DevState S, int k,
+                                                                           const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;
   const int lane = threadIdx.x;
   const int tile = blockIdx.y;

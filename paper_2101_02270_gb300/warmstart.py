@@ -80,6 +80,21 @@ class MLP:
     def error(self):
         return lib.pf_mlp_error(self._h)
 
+    # ---- checkpoint / resume (weights and standardisation; the optimiser
+    # state restarts) ----
+    def save(self, path, norm=None):
+        arrs = self.params()
+        extra = {} if norm is None else {f"norm{i}": np.asarray(v, np.float32) for i, v in enumerate(norm)}
+        np.savez(path, shape=np.array(self.shape), **{f"p{i}": a for i, a in enumerate(arrs)}, **extra)
+
+    def load(self, path):
+        z = np.load(path)
+        if tuple(int(v) for v in z["shape"]) != tuple(self.shape):
+            raise ValueError(f"checkpoint shape {tuple(z['shape'])} != network {self.shape}")
+        self.set_params([z[f"p{i}"] for i in range(6)])
+        if "norm0" in z:
+            self.set_norm(*[z[f"norm{i}"] for i in range(4)])
+
 
 def gemm_bf16(A, B, variant=1):
     """C = A B^T on the tensor cores (A [M,K], B [N,K] bfloat16 CUDA tensors).

@@ -123,3 +123,17 @@ def test_warm_start_gain_on_2000_bus_grid():
     _, pv, pq, _ = nrpf.bus_sets(g.bus_type)
     F = nrpf.mismatch(Y, vw[0].cpu().numpy(), Sh[0].cpu().numpy(), pv, pq)
     assert np.max(np.abs(F)) < 1e-8
+
+
+def test_mlp_checkpoint_roundtrip(tmp_path):
+    ws = _ws()
+    a = ws.MLP(64, 128, 128, 40, bmax=64, seed=5)
+    b = ws.MLP(64, 128, 128, 40, bmax=64, seed=6)
+    norm = [np.full(64, 0.5), np.full(64, 2.0), np.zeros(40), np.ones(40)]
+    a.set_norm(*norm)
+    a.save(tmp_path / "w.npz", norm=norm)
+    b.load(tmp_path / "w.npz")
+    X = torch.from_numpy(np.random.default_rng(0).standard_normal((16, 64)).astype(np.float32)).cuda()
+    assert torch.equal(a.predict(X), b.predict(X))
+    for p, q in zip(a.params(), b.params()):
+        assert np.array_equal(p, q)
