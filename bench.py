@@ -63,8 +63,8 @@ def parse_args():
     ap.add_argument("--batch", type=int, default=0, help="override the batch size (0 = the workload's)")
     ap.add_argument("--lu", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--maxit", type=int, default=MAXIT)
-    ap.add_argument("--dense-frac", type=float, default=0.7)
-    ap.add_argument("--panel", type=int, default=8)
+    ap.add_argument("--dense-frac", type=float, default=0.0, help="0 = the library's default for the precision")
+    ap.add_argument("--panel", type=int, default=0, help="0 = the library's default for the precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-all", action="store_true",
                     help="diagnostic: CUDA-event timing of every kernel class (adds two events per launch)")
@@ -592,14 +592,15 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (dense trailing update) ----
     w = 8 if args.lu == "fp64" else 4
     ndp = info["dense_pad"]
+    kb = args.panel or (16 if args.lu == "fp32" else 8)
     refactors = int(iters.sum()) * args.steps  # one refactor per Newton update per instance
     du = prof["dense_update"]
-    du_flop = dense_update_flop(ndp, args.panel) * refactors
+    du_flop = dense_update_flop(ndp, kb) * refactors
     achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
     peak = fp64_peak if args.lu == "fp64" else fp32_peak
-    r2 = [(ndp - k - args.panel) ** 2 for k in range(0, ndp, args.panel) if ndp - k - args.panel > 0]
+    r2 = [(ndp - k - kb) ** 2 for k in range(0, ndp, kb) if ndp - k - kb > 0]
     traffic = (DENSE_UPDATE_DRAM_B_PER_R2 * B * sum(r2) / len(r2)
-               if r2 and args.lu == "fp64" and args.panel == 8 else None)
+               if r2 and args.lu == "fp64" and kb == 8 else None)
     hbm, hbm_kind = measured_hbm()
     # whole-step HBM roofline (metric's second half): algorithmic bytes per
     # instance-iteration = LU written once and read once + voltages, injections,
@@ -616,7 +617,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": name, "batch_per_gpu": B, "buses": g.n, "branches": g.n_branch,
                    "unknowns": info["m"], "lu_precision": args.lu, "tol": TOL, "maxit": args.maxit,
-                   "load_scale": g.load_scale, "dense_block": info["dense_dim"], "panel": args.panel,
+                   "load_scale": g.load_scale, "dense_block": info["dense_dim"], "panel": kb,
                    "parallelism": f"instances split over {world} GPU(s)",
                    "l2": f"working set > L2: LU workspace {nnz_lu * w * B / 1e9:.1f} GB per GPU",
                    "plan_ms": round(plan_ms, 1)},

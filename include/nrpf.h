@@ -57,8 +57,10 @@ typedef struct pf_options {
   int ordering;        /* NRPF_ORDER_AMD | NRPF_ORDER_NATURAL                      */
   double dense_frac;   /* AMD stops once the cheapest vertex touches this share of
                           the remaining unknowns; the rest is one dense block.
-                          0 selects the default (0.7); >= 1 disables the block. */
-  int panel;           /* dense-block panel width (4, 8 or 16); 0 = default 8      */
+                          0 selects the default (0.7 for FP64 LU, 0.3 for FP32
+                          LU); >= 1 disables the block. */
+  int panel;           /* dense-block panel width (4, 8 or 16); 0 = default (8 for
+                          FP64 LU, 16 for FP32 LU)                               */
   int max_batch;       /* batch capacity to allocate at plan creation; 0 = grow on
                           first solve (that call then allocates device memory)    */
   int host_only;       /* 1: symbolic analysis only, no device memory; the plan
@@ -86,8 +88,8 @@ typedef struct pf_plan_info {
   int lu_precision;
 } pf_plan_info;
 
-/* Fill pf_options with the defaults (AMD ordering, FP64 LU, dense_frac 0.7,
- * panel 8, grow-on-demand workspace, device upload). */
+/* Fill pf_options with the defaults (AMD ordering, FP64 LU, dense_frac and
+ * panel chosen by precision, grow-on-demand workspace, device upload). */
 int pf_options_default(pf_options* opt);
 
 /* Assemble Ybus (MATPOWER pi-model convention, Sec. 3) from branch data.

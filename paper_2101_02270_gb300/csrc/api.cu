@@ -161,8 +161,8 @@ int pf_options_default(pf_options* opt) {
   if (!opt) return NRPF_ERR_ARG;
   opt->lu_precision = NRPF_LU_FP64;
   opt->ordering = NRPF_ORDER_AMD;
-  opt->dense_frac = 0.7;
-  opt->panel = 8;
+  opt->dense_frac = 0.0;  /* chosen by precision at plan creation */
+  opt->panel = 0;  /* chosen by precision at plan creation */
   opt->max_batch = 0;
   opt->host_only = 0;
   return NRPF_OK;
@@ -216,11 +216,15 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
   *out = nullptr;
   pf_options o;
   pf_options_default(&o);
-  if (opt) {
-    o = *opt;
-    if (o.dense_frac == 0.0) o.dense_frac = 0.7;
-    if (o.panel == 0) o.panel = 8;
-  }
+  if (opt) o = *opt;
+  // default panel width by precision: FP32 needs the wider panel to feed its
+  // FMA pipes with fewer passes over the trailing block
+  if (o.panel == 0) o.panel = o.lu_precision == NRPF_LU_FP32 ? 16 : 8;
+  // default dense cut by LU precision: an FMA of the sparse phase costs about
+  // twice a dense-block FMA in FP64 (the FP64 pipe bounds both) but about 13x
+  // in FP32 (the dense block runs at FP32 rate, the sparse phase does not),
+  // so the FP32 path hands more of the matrix to the dense block
+  if (o.dense_frac == 0.0) o.dense_frac = o.lu_precision == NRPF_LU_FP32 ? 0.3 : 0.7;
   if (o.lu_precision != NRPF_LU_FP64 && o.lu_precision != NRPF_LU_FP32) return NRPF_ERR_ARG;
   if (o.ordering != NRPF_ORDER_AMD && o.ordering != NRPF_ORDER_NATURAL) return NRPF_ERR_ARG;
   if (!(o.dense_frac > 0.0) || o.max_batch < 0) return NRPF_ERR_ARG;

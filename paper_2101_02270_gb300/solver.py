@@ -32,7 +32,7 @@ class Plan:
     """Symbolic plan for one Ybus sparsity pattern (pf_plan_create)."""
 
     def __init__(self, n, rowptr, colidx, y_re, y_im, bus_type, lu_precision="fp64",
-                 ordering="amd", dense_frac=0.7, panel=8, max_batch=0, host_only=False):
+                 ordering="amd", dense_frac=0.0, panel=0, max_batch=0, host_only=False):
         self.n = int(n)
         self._rowptr = np.ascontiguousarray(rowptr, np.int32)
         self._colidx = np.ascontiguousarray(colidx, np.int32)
