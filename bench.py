@@ -598,10 +598,14 @@ def run_ours(args):
     du_flop = dense_update_flop(ndp, kb) * refactors
     achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
     peak = fp64_peak if args.lu == "fp64" else fp32_peak
+    hbm, hbm_kind = measured_hbm()
+    # algorithmic bytes of the trailing updates: the trailing block read and
+    # written once per panel, plus the two panels, per refactor
+    du_bytes = sum(2 * w * (ndp - k - kb) ** 2 + 2 * w * kb * (ndp - k - kb)
+                   for k in range(0, ndp, kb) if ndp - k - kb > 0) * refactors
     r2 = [(ndp - k - kb) ** 2 for k in range(0, ndp, kb) if ndp - k - kb > 0]
     traffic = (DENSE_UPDATE_DRAM_B_PER_R2 * B * sum(r2) / len(r2)
                if r2 and args.lu == "fp64" and kb == 8 else None)
-    hbm, hbm_kind = measured_hbm()
     # whole-step HBM roofline (metric's second half): algorithmic bytes per
     # instance-iteration = LU written once and read once + voltages, injections,
     # rhs and solution
@@ -624,12 +628,18 @@ def run_ours(args):
         "iterations": {"mean": float(iters.mean()), "max": int(iters.max()),
                        "hist": np.bincount(iters).tolist()},
         "converged": conv, "failed": int(np.sum(status == 2)),
-        "roofline": {"bound": "alu", "kernel": "dense_update", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "peak_kind": ("measured FP64" if args.lu == "fp64" else "measured FP32")
-                     + " FMA-chain throughput (pf_fma_peak)",
-                     "traffic_kind": "ncu DRAM bytes per average active launch, scaled from a batch-640 capture",
-                     "launches": du[0], "ms_total": du[2]},
+        "roofline": ({"bound": "alu", "kernel": "dense_update", "achieved": achieved, "peak": peak,
+                      "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                      "peak_kind": "measured FP64 FMA-chain throughput (pf_fma_peak)",
+                      "traffic_kind": "ncu DRAM bytes per average active launch, scaled from a batch-640 capture",
+                      "launches": du[0], "ms_total": du[2]}
+                     if args.lu == "fp64" else
+                     {"bound": "hbm", "kernel": "dense_update",
+                      "achieved": du_bytes / (du[2] / 1e3) / 1e9 if du[2] > 0 else None, "peak": hbm,
+                      "unit": "GB/s", "frac": (du_bytes / (du[2] / 1e3) / 1e9 / hbm) if du[2] > 0 else None,
+                      "traffic": None, "peak_kind": f"{hbm_kind} HBM copy bandwidth",
+                      "fp32_tflops": achieved, "fp32_peak_tflops": fp32_peak,
+                      "launches": du[0], "ms_total": du[2]}),
         "hbm_roofline": {"algorithmic_bytes_per_instance_iteration": bmin,
                          "achieved_gbs": step_bytes * args.steps / (ms_max / 1e3) / 1e9,
                          "peak_gbs": hbm, "peak_kind": hbm_kind, "pct": hbm_pct},

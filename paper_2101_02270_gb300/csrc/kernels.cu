@@ -21,6 +21,33 @@ __device__ __forceinline__ bool tile_active(const DevState& S, int tile, int lan
   return __any_sync(0xffffffffu, S.active[tile * kTile + lane] != 0);
 }
 
+// Layout of the dense block inside a tile's LU array.  FP64: element (r, c)
+// of the ndp x ndp block at (c * ndp + r) * 32 + lane.  FP32: four
+// consecutive rows of a column stay together per lane,
+// (c * ndp + (r & ~3)) * 32 + lane * 4 + (r & 3), so a lane reads rows
+// r..r+3 (r % 4 == 0) as one 16-byte vector and a warp's access is still one
+// contiguous 512-byte segment.  ndp is a multiple of the panel width (>= 4).
+template <typename T>
+struct DenseGroup {
+  static constexpr int G = sizeof(T) == 4 ? 4 : 1;
+};
+
+template <typename T>
+__device__ __forceinline__ size_t dense_off(int r, int c, int ld, int lane) {
+  constexpr int G = DenseGroup<T>::G;
+  return ((size_t)c * ld + (r & ~(G - 1))) * kTile + (size_t)lane * G + (r & (G - 1));
+}
+
+// offset of LU position p of lane `lane` within its tile's array (positions
+// >= NS are in the dense block)
+template <typename T>
+__device__ __forceinline__ size_t lu_off(int64_t p, int64_t NS, int lane) {
+  constexpr int G = DenseGroup<T>::G;
+  if (G == 1 || p < NS) return (size_t)p * kTile + lane;
+  const int64_t q = p - NS;
+  return (size_t)NS * kTile + (size_t)(q & ~(int64_t)(G - 1)) * kTile + (size_t)lane * G + (size_t)(q & (G - 1));
+}
+
 // ---------------------------------------------------------------------------
 // Input / output transposes: user [B, n] complex128 <-> interleaved tiles
 // (the paper's "transpose to batch" step on the device, Sec. 3.2).
@@ -148,10 +175,10 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
           const double Wr = ei * yr + fi * yi;
           const double Wi = fi * yr - ei * yi;
           const double ik = vinv[k * kTile + lane];
-          LU[(size_t)jm.x * kTile + lane] = (T)Wi;
-          if (jm.y >= 0) LU[(size_t)jm.y * kTile + lane] = (T)(Wr * ik);
-          if (jm.z >= 0) LU[(size_t)jm.z * kTile + lane] = (T)(-Wr);
-          if (jm.w >= 0) LU[(size_t)jm.w * kTile + lane] = (T)(Wi * ik);
+          LU[lu_off<T>(jm.x, P.NS, lane)] = (T)Wi;
+          if (jm.y >= 0) LU[lu_off<T>(jm.y, P.NS, lane)] = (T)(Wr * ik);
+          if (jm.z >= 0) LU[lu_off<T>(jm.z, P.NS, lane)] = (T)(-Wr);
+          if (jm.w >= 0) LU[lu_off<T>(jm.w, P.NS, lane)] = (T)(Wi * ik);
         }
       }
     }
@@ -176,10 +203,10 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
       const double vm2 = ei * ei + fi * fi;
       const double ivm = vinv[o];
       const double vm = vm2 * ivm;
-      LU[(size_t)jm.x * kTile + lane] = (T)(-Qc - Bv * vm2);
-      if (jm.y >= 0) LU[(size_t)jm.y * kTile + lane] = (T)(Pc * ivm + G * vm);
-      if (jm.z >= 0) LU[(size_t)jm.z * kTile + lane] = (T)(Pc - G * vm2);
-      if (jm.w >= 0) LU[(size_t)jm.w * kTile + lane] = (T)(Qc * ivm - Bv * vm);
+      LU[lu_off<T>(jm.x, P.NS, lane)] = (T)(-Qc - Bv * vm2);
+      if (jm.y >= 0) LU[lu_off<T>(jm.y, P.NS, lane)] = (T)(Pc * ivm + G * vm);
+      if (jm.z >= 0) LU[lu_off<T>(jm.z, P.NS, lane)] = (T)(Pc - G * vm2);
+      if (jm.w >= 0) LU[lu_off<T>(jm.w, P.NS, lane)] = (T)(Qc * ivm - Bv * vm);
     }
   }
   // NaN -> +inf so that the unsigned-integer max keeps it
@@ -243,7 +270,7 @@ __global__ void k_set_ones(DevPlan P, DevState S, const int32_t* __restrict__ ga
   T* LU = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;
   T* X = reinterpret_cast<T*>(S.x) + (size_t)tile * P.mp * kTile;
   for (int t = threadIdx.y; t < P.n_one; t += blockDim.y) {
-    LU[(size_t)P.one_pos[t] * kTile + lane] = (T)1;
+    LU[lu_off<T>(P.one_pos[t], P.NS, lane)] = (T)1;
     X[(size_t)(P.m + t) * kTile + lane] = (T)0;
   }
 }
@@ -267,7 +294,9 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
   const int tile = blockIdx.y;
   if (ci >= c1) return;
   if (!tile_active(S, tile, lane)) return;
-  T* __restrict__ LU = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile + lane;
+  T* __restrict__ LUb = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;  // tile base
+  T* __restrict__ LU = LUb + lane;  // sparse positions (< NS): p * 32
+  const int64_t NS = P.NS;
   const int j = P.lu_cols[ci];
   const int u0 = P.col_upd_ptr[j], u1 = P.col_upd_ptr[j + 1];
   for (int u = u0; u < u1; ++u) {
@@ -277,20 +306,18 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
     const T* __restrict__ src = LU + (size_t)up.lsrc * kTile;
     int q = 0;
     for (; q + 4 <= up.llen; q += 4) {
-      const int d0 = dst[q], d1 = dst[q + 1], d2 = dst[q + 2], d3 = dst[q + 3];
+      const size_t o0 = lu_off<T>(dst[q], NS, lane), o1 = lu_off<T>(dst[q + 1], NS, lane);
+      const size_t o2 = lu_off<T>(dst[q + 2], NS, lane), o3 = lu_off<T>(dst[q + 3], NS, lane);
       const T s0 = src[(size_t)q * kTile], s1 = src[(size_t)(q + 1) * kTile];
       const T s2 = src[(size_t)(q + 2) * kTile], s3 = src[(size_t)(q + 3) * kTile];
-      const T a0 = LU[(size_t)d0 * kTile], a1 = LU[(size_t)d1 * kTile];
-      const T a2 = LU[(size_t)d2 * kTile], a3 = LU[(size_t)d3 * kTile];
-      LU[(size_t)d0 * kTile] = a0 - x * s0;
-      LU[(size_t)d1 * kTile] = a1 - x * s1;
-      LU[(size_t)d2 * kTile] = a2 - x * s2;
-      LU[(size_t)d3 * kTile] = a3 - x * s3;
+      const T a0 = LUb[o0], a1 = LUb[o1];
+      const T a2 = LUb[o2], a3 = LUb[o3];
+      LUb[o0] = a0 - x * s0;
+      LUb[o1] = a1 - x * s1;
+      LUb[o2] = a2 - x * s2;
+      LUb[o3] = a3 - x * s3;
     }
-    for (; q < up.llen; ++q) {
-      const int d = dst[q];
-      LU[(size_t)d * kTile] -= x * src[(size_t)q * kTile];
-    }
+    for (; q < up.llen; ++q) LUb[lu_off<T>(dst[q], NS, lane)] -= x * src[(size_t)q * kTile];
   }
   const int dpj = P.dp[j];
   if (dpj >= 0) {
@@ -317,14 +344,14 @@ __global__ void k_dense_diag(DevPlan P, DevState S, int k, const int32_t* __rest
   const int tile = blockIdx.x * blockDim.y + threadIdx.y;
   if (tile * kTile >= S.Bp) return;
   if (!tile_active(S, tile, lane)) return;
-  T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
+  T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile;  // dense block
   T* __restrict__ inv = reinterpret_cast<T*>(S.inv) + (size_t)tile * KB * kTile + lane;
   const int ld = P.ndp;
   T D[KB][KB];
 #pragma unroll
   for (int c = 0; c < KB; ++c)
 #pragma unroll
-    for (int r = 0; r < KB; ++r) D[r][c] = A[((size_t)(k + c) * ld + (k + r)) * kTile];
+    for (int r = 0; r < KB; ++r) D[r][c] = A[dense_off<T>(k + r, k + c, ld, lane)];
 #pragma unroll
   for (int c = 0; c < KB; ++c) {
     const T ip = (T)1 / D[c][c];
@@ -339,7 +366,7 @@ __global__ void k_dense_diag(DevPlan P, DevState S, int k, const int32_t* __rest
 #pragma unroll
   for (int c = 0; c < KB; ++c)
 #pragma unroll
-    for (int r = 0; r < KB; ++r) A[((size_t)(k + c) * ld + (k + r)) * kTile] = D[r][c];
+    for (int r = 0; r < KB; ++r) A[dense_off<T>(k + r, k + c, ld, lane)] = D[r][c];
 }
 
 template <typename T, int KB>
@@ -353,9 +380,9 @@ __global__ void k_dense_panel(DevPlan P, DevState S, int k, const int32_t* __res
   const int ngrp = (ld - r0) / 4;   // groups of four rows (and of four columns)
   const int g = blockIdx.x * blockDim.y + threadIdx.y;
   if (g >= 2 * ngrp) return;
-  T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
+  T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile;  // dense block
   const T* __restrict__ inv = reinterpret_cast<const T*>(S.inv) + (size_t)tile * KB * kTile + lane;
-  auto at = [&](int r, int c) -> T& { return A[((size_t)c * ld + r) * kTile]; };
+  auto at = [&](int r, int c) -> T& { return A[dense_off<T>(r, c, ld, lane)]; };
   if (g < ngrp) {
     // rows i0..i0+3: x U11 = a  (U11 upper, pivots inverted)
     const int i0 = r0 + 4 * g;
@@ -424,35 +451,98 @@ __global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevP
   if (t >= nb * nb) return;
   const int bi = t % nb, bj = t / nb;
   const int i0 = r0 + TS * bi, j0 = r0 + TS * bj;
-  T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
-  // element (r, c) of the block is A[(c * ld + r) * 32]; rows of one column
-  // are 32 elements apart, so every access below is a column pointer plus a
-  // compile-time offset
-  const size_t cstride = (size_t)ld * kTile;
-  T* __restrict__ cj = A + (size_t)j0 * cstride + (size_t)i0 * kTile;  // (i0, j0)
-  const T* __restrict__ pa = A + (size_t)k * cstride + (size_t)i0 * kTile;  // (i0, k)
-  const T* __restrict__ pb = A + (size_t)j0 * cstride + (size_t)k * kTile;  // (k, j0)
+  T* __restrict__ Ab = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile;  // dense block
   T acc[TS][TS];
-#pragma unroll
-  for (int c = 0; c < TS; ++c)
-#pragma unroll
-    for (int r = 0; r < TS; ++r) acc[r][c] = cj[c * cstride + r * kTile];
-#pragma unroll
-  for (int p = 0; p < KB; ++p) {
-    T a[TS], b[TS];
-#pragma unroll
-    for (int r = 0; r < TS; ++r) a[r] = pa[p * cstride + r * kTile];
-#pragma unroll
-    for (int c = 0; c < TS; ++c) b[c] = pb[c * cstride + p * kTile];
+  if constexpr (DenseGroup<T>::G == 4 && TS == 8) {
+    // FP32, grouped rows: rows r..r+3 of column c for this lane are the
+    // float4 at index (c * ld + r) * 8 + lane
+    float4* __restrict__ A4 = reinterpret_cast<float4*>(Ab);
 #pragma unroll
     for (int c = 0; c < TS; ++c)
 #pragma unroll
-      for (int r = 0; r < TS; ++r) acc[r][c] -= a[r] * b[c];
+      for (int h = 0; h < 2; ++h) {
+        const float4 v = A4[((size_t)(j0 + c) * ld + i0 + 4 * h) * 8 + lane];
+        acc[4 * h][c] = v.x;
+        acc[4 * h + 1][c] = v.y;
+        acc[4 * h + 2][c] = v.z;
+        acc[4 * h + 3][c] = v.w;
+      }
+#pragma unroll
+    for (int pp = 0; pp < KB / 4; ++pp) {
+      float4 bq[TS];  // rows k+4pp .. k+4pp+3 of columns j0 .. j0+7 (U12)
+#pragma unroll
+      for (int c = 0; c < TS; ++c) bq[c] = A4[((size_t)(j0 + c) * ld + k + 4 * pp) * 8 + lane];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int p = 4 * pp + q;
+        const float4 a0 = A4[((size_t)(k + p) * ld + i0) * 8 + lane];  // rows i0..i0+7 of column k+p (L21)
+        const float4 a1 = A4[((size_t)(k + p) * ld + i0 + 4) * 8 + lane];
+        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+        for (int c = 0; c < TS; ++c) {
+          const float b = q == 0 ? bq[c].x : q == 1 ? bq[c].y : q == 2 ? bq[c].z : bq[c].w;
+#pragma unroll
+          for (int r = 0; r < TS; ++r) acc[r][c] -= a[r] * b;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < TS; ++c)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        A4[((size_t)(j0 + c) * ld + i0 + 4 * h) * 8 + lane] =
+            make_float4(acc[4 * h][c], acc[4 * h + 1][c], acc[4 * h + 2][c], acc[4 * h + 3][c]);
+  } else if constexpr (DenseGroup<T>::G == 1) {
+    // element (r, c) is Ab[(c * ld + r) * 32 + lane]: a column pointer plus a
+    // compile-time offset for every access
+    T* __restrict__ A = Ab + lane;
+    const size_t cstride = (size_t)ld * kTile;
+    T* __restrict__ cj = A + (size_t)j0 * cstride + (size_t)i0 * kTile;      // (i0, j0)
+    const T* __restrict__ pa = A + (size_t)k * cstride + (size_t)i0 * kTile;  // (i0, k)
+    const T* __restrict__ pb = A + (size_t)j0 * cstride + (size_t)k * kTile;  // (k, j0)
+#pragma unroll
+    for (int c = 0; c < TS; ++c)
+#pragma unroll
+      for (int r = 0; r < TS; ++r) acc[r][c] = cj[c * cstride + r * kTile];
+#pragma unroll
+    for (int p = 0; p < KB; ++p) {
+      T a[TS], b[TS];
+#pragma unroll
+      for (int r = 0; r < TS; ++r) a[r] = pa[p * cstride + r * kTile];
+#pragma unroll
+      for (int c = 0; c < TS; ++c) b[c] = pb[c * cstride + p * kTile];
+#pragma unroll
+      for (int c = 0; c < TS; ++c)
+#pragma unroll
+        for (int r = 0; r < TS; ++r) acc[r][c] -= a[r] * b[c];
+    }
+#pragma unroll
+    for (int c = 0; c < TS; ++c)
+#pragma unroll
+      for (int r = 0; r < TS; ++r) cj[c * cstride + r * kTile] = acc[r][c];
+  } else {
+    // grouped layout with a 4x4 tile (FP32 with panel 4): element by element
+#pragma unroll
+    for (int c = 0; c < TS; ++c)
+#pragma unroll
+      for (int r = 0; r < TS; ++r) acc[r][c] = Ab[dense_off<T>(i0 + r, j0 + c, ld, lane)];
+#pragma unroll
+    for (int p = 0; p < KB; ++p) {
+      T a[TS], b[TS];
+#pragma unroll
+      for (int r = 0; r < TS; ++r) a[r] = Ab[dense_off<T>(i0 + r, k + p, ld, lane)];
+#pragma unroll
+      for (int c = 0; c < TS; ++c) b[c] = Ab[dense_off<T>(k + p, j0 + c, ld, lane)];
+#pragma unroll
+      for (int c = 0; c < TS; ++c)
+#pragma unroll
+        for (int r = 0; r < TS; ++r) acc[r][c] -= a[r] * b[c];
+    }
+#pragma unroll
+    for (int c = 0; c < TS; ++c)
+#pragma unroll
+      for (int r = 0; r < TS; ++r) Ab[dense_off<T>(i0 + r, j0 + c, ld, lane)] = acc[r][c];
   }
-#pragma unroll
-  for (int c = 0; c < TS; ++c)
-#pragma unroll
-    for (int r = 0; r < TS; ++r) cj[c * cstride + r * kTile] = acc[r][c];
 }
 
 // ---------------------------------------------------------------------------
@@ -510,7 +600,14 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_dense_solve_smem(DevPlan P
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int tile = blockIdx.x;
   if (!__syncthreads_or(S.active[tile * kTile + lane])) return;
-  const T* __restrict__ A = reinterpret_cast<const T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile + lane;
+  const T* __restrict__ Ab = reinterpret_cast<const T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile;
+  const size_t cstride = (size_t)P.ndp * kTile;
+  auto A = [&](int r, int c) -> T {
+    if constexpr (DenseGroup<T>::G == 1)
+      return Ab[(size_t)c * cstride + (size_t)r * kTile + lane];
+    else
+      return Ab[dense_off<T>(r, c, P.ndp, lane)];
+  };
   T* __restrict__ X = reinterpret_cast<T*>(S.x) + ((size_t)tile * P.mp + P.s) * kTile + lane;
   const int ld = P.ndp;
   // the tile's right-hand side: in shared memory when it fits, else in place
@@ -527,7 +624,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_dense_solve_smem(DevPlan P
         const T xc = xs[(k0 + c) * kTile + lane];
 #pragma unroll
         for (int r = c + 1; r < SB; ++r)
-          xs[(k0 + r) * kTile + lane] -= A[((size_t)(k0 + c) * ld + k0 + r) * kTile] * xc;
+          xs[(k0 + r) * kTile + lane] -= A(k0 + r, k0 + c) * xc;
       }
     }
     __syncthreads();
@@ -537,7 +634,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_dense_solve_smem(DevPlan P
     for (int r = k0 + SB + warp; r < ld; r += kSolveWarps) {
       T acc = xs[r * kTile + lane];
 #pragma unroll
-      for (int c = 0; c < SB; ++c) acc -= A[((size_t)(k0 + c) * ld + r) * kTile] * xb[c];
+      for (int c = 0; c < SB; ++c) acc -= A(r, k0 + c) * xb[c];
       xs[r * kTile + lane] = acc;
     }
     __syncthreads();
@@ -546,10 +643,10 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_dense_solve_smem(DevPlan P
     if (warp == 0) {
 #pragma unroll
       for (int c = SB - 1; c >= 0; --c) {
-        const T xc = xs[(k0 + c) * kTile + lane] / A[((size_t)(k0 + c) * ld + k0 + c) * kTile];
+        const T xc = xs[(k0 + c) * kTile + lane] / A(k0 + c, k0 + c);
         xs[(k0 + c) * kTile + lane] = xc;
 #pragma unroll
-        for (int r = 0; r < c; ++r) xs[(k0 + r) * kTile + lane] -= A[((size_t)(k0 + c) * ld + k0 + r) * kTile] * xc;
+        for (int r = 0; r < c; ++r) xs[(k0 + r) * kTile + lane] -= A(k0 + r, k0 + c) * xc;
       }
     }
     __syncthreads();
@@ -559,7 +656,7 @@ __global__ void __launch_bounds__(32 * kSolveWarps) k_dense_solve_smem(DevPlan P
     for (int r = warp; r < k0; r += kSolveWarps) {
       T acc = xs[r * kTile + lane];
 #pragma unroll
-      for (int c = 0; c < SB; ++c) acc -= A[((size_t)(k0 + c) * ld + r) * kTile] * xb[c];
+      for (int c = 0; c < SB; ++c) acc -= A(r, k0 + c) * xb[c];
       xs[r * kTile + lane] = acc;
     }
     __syncthreads();
@@ -653,8 +750,8 @@ __global__ void k_lu_out(DevPlan P, DevState S, int B, const int64_t* __restrict
   if (q >= nnz) return;
   const int b = tile * kTile + lane;
   if (b >= B) return;
-  const T* LU = reinterpret_cast<const T*>(S.lu) + (size_t)tile * P.NLU * kTile + lane;
-  out[(size_t)b * nnz + q] = (double)LU[(size_t)map[q] * kTile];
+  const T* LU = reinterpret_cast<const T*>(S.lu) + (size_t)tile * P.NLU * kTile;
+  out[(size_t)b * nnz + q] = (double)LU[lu_off<T>(map[q], P.NS, lane)];
 }
 
 }  // namespace

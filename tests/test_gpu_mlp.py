@@ -137,3 +137,29 @@ def test_mlp_checkpoint_roundtrip(tmp_path):
     assert torch.equal(a.predict(X), b.predict(X))
     for p, q in zip(a.params(), b.params()):
         assert np.array_equal(p, q)
+
+
+def test_warm_start_falls_back_to_flat_start():
+    """A network whose guesses are useless (angles far off) makes Newton fail
+    from them; those instances are re-solved from flat start and reach the
+    flat-start solutions."""
+    import paper_2101_02270_gb300 as pf
+    ws = _ws()
+    g = gridgen.make_grid("mesh30_b64")
+    plan = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type)
+    nns = int(np.sum(g.bus_type != 3))
+    net = ws.MLP(2 * g.n, 128, 128, 2 * nns, bmax=64, seed=0)
+    arrs = [np.zeros_like(a) for a in net.params()]
+    arrs[5][:nns] = 0.05            # |V| guess of 0.05 p.u. (far from the solution)
+    arrs[5][nns:] = 3.0             # angles of 3 rad
+    net.set_params(arrs)
+    w = ws.WarmStart(plan, g.bus_type, net)
+    sc = gridgen.config_scenarios("mesh30_b64", g, batch=64)
+    S = torch.from_numpy(sc.sbus(g)).cuda()
+    Vf = torch.from_numpy(sc.v0_flat(g)).cuda()
+    v, it, st, fb = w.solve(S, Vf, 1e-8, 10)
+    vf, itf, stf = plan.solve(S, Vf, 1e-8, 10)
+    assert bool((st == 0).all())
+    assert int(fb.sum()) > 0
+    # every fallback instance equals the flat-start result exactly
+    assert torch.equal(v[fb], vf[fb]) and torch.equal(it[fb], itf[fb])
