@@ -59,8 +59,11 @@ typedef struct pf_options {
                           the remaining unknowns; the rest is one dense block.
                           0 selects the default (0.7 for FP64 LU, 0.3 for FP32
                           LU); >= 1 disables the block. */
-  int panel;           /* dense-block panel width (4, 8 or 16); 0 = default (8 for
-                          FP64 LU, 16 for FP32 LU)                               */
+  int panel;           /* dense-block panel width: 4, 8 or 16 (one trailing
+                          update per panel), or 32 / 64 (an outer panel
+                          factorised in steps of 16, then one trailing update
+                          per outer panel); 0 = default (8 for FP64 LU, 64 for
+                          FP32 LU)                                               */
   int max_batch;       /* batch capacity to allocate at plan creation; 0 = grow on
                           first solve (that call then allocates device memory)    */
   int host_only;       /* 1: symbolic analysis only, no device memory; the plan
@@ -86,6 +89,7 @@ typedef struct pf_plan_info {
   double solve_fma;    /* multiply-adds of one FS/BS, one instance                */
   int capacity;        /* batch capacity currently allocated                     */
   int lu_precision;
+  int panel;           /* dense-block panel width in use                          */
 } pf_plan_info;
 
 /* Fill pf_options with the defaults (AMD ordering, FP64 LU, dense_frac and

@@ -34,7 +34,7 @@ class pf_plan_info(C.Structure):
                 ("nnz_lu", C.c_int64), ("sparse_cols", C.c_int), ("dense_dim", C.c_int),
                 ("dense_pad", C.c_int), ("lu_levels", C.c_int), ("fwd_levels", C.c_int),
                 ("bwd_levels", C.c_int), ("lu_fma", C.c_double), ("solve_fma", C.c_double),
-                ("capacity", C.c_int), ("lu_precision", C.c_int)]
+                ("capacity", C.c_int), ("lu_precision", C.c_int), ("panel", C.c_int)]
 
 
 NKCLASSES = 16

@@ -1,5 +1,6 @@
 // C ABI of the batched Newton-Raphson power-flow library (include/nrpf.h).
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -43,7 +44,29 @@ int upload(pf_plan* p, const std::vector<T>& v, const T** out) {
   return NRPF_OK;
 }
 
+// Fold the launches made by loop graphs (one body's launches x bodies run)
+// into the counters and zero the device count.  Synchronises the device.
+void fold_graph_launches(pf_plan* p) {
+  if (!p->st.ctl) return;
+  cudaDeviceSynchronize();
+  long long gi = 0;
+  char* f = reinterpret_cast<char*>(p->st.ctl) + offsetof(nrpf::SolveCtl, graph_iters);
+  if (cudaMemcpy(&gi, f, sizeof(gi), cudaMemcpyDeviceToHost) != cudaSuccess) return;
+  for (int c = 0; c < nrpf::K_NCLASS; ++c) p->rec.launches[c] += p->body_launches[c] * gi;
+  const long long zero = 0;
+  cudaMemcpy(f, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+}
+
+void destroy_loop_graph(pf_plan* p) {
+  if (p->loop_exec) cudaGraphExecDestroy(p->loop_exec);
+  if (p->loop_graph) cudaGraphDestroy(p->loop_graph);
+  p->loop_exec = nullptr;
+  p->loop_graph = nullptr;
+}
+
 void free_ws(pf_plan* p) {
+  fold_graph_launches(p);
+  destroy_loop_graph(p);
   for (void* a : p->ws_allocs) cudaFree(a);
   p->ws_allocs.clear();
   p->capacity = 0;
@@ -88,37 +111,116 @@ int ensure_capacity(pf_plan* p, int B) {
   AL((size_t)Bp * 4, status, int32_t*);
   AL((size_t)Bp * 4, active, int32_t*);
   AL((size_t)Bp * 4, bad, int32_t*);
-  AL(2 * 4, n_active, int32_t*);
+  AL(sizeof(nrpf::SolveCtl), ctl, nrpf::SolveCtl*);
 #undef AL
+  CK(cudaMemset(s.ctl, 0, sizeof(nrpf::SolveCtl)));
+  if (!p->h_prev) CK(cudaHostAlloc(reinterpret_cast<void**>(&p->h_prev), sizeof(int32_t), cudaHostAllocDefault));
   p->st = s;
   p->capacity = Bp;
   return NRPF_OK;
 }
 
+// One Newton iteration (Alg. 1 loop body): LU preparation and mismatch +
+// Jacobian (gated by the previous check), the convergence test, then
+// refactorisation, FS/BS and update (gated by this check), and the tail that
+// advances the loop control.
 template <typename T>
-void enqueue_solve(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
-                   double* v_out, int32_t* iters, uint8_t* status, cudaStream_t st) {
+void enqueue_body(pf_plan* p, cudaStream_t st, nrpf::Recorder* rec, cudaGraphConditionalHandle cond, int graph) {
   const DevPlan& P = p->dp;
   const DevState& S = p->st;
   const HostPlan& h = p->hp;
+  const int32_t* prev = nrpf::ctl_prev(S);
+  const int32_t* cur = nrpf::ctl_cur(S);
+  nrpf::launch_prepare_lu<T>(P, S, prev, st, rec);
+  nrpf::launch_mismatch<T>(P, S, 1, prev, st, rec);
+  nrpf::launch_check(S, st, rec);
+  nrpf::launch_factor<T>(P, S, h.lu_lvl_ptr, cur, st, rec);
+  nrpf::launch_solve<T>(P, S, h.fw_lvl_ptr, h.bw_lvl_ptr, cur, st, rec);
+  nrpf::launch_update<T>(P, S, cur, st, rec);
+  nrpf::launch_iter_tail(S, cond, graph, st, rec);
+}
+
+// The loop graph: a WHILE node whose body is one iteration, captured once per
+// workspace; the iteration's tail kernel sets the condition, so the loop ends
+// on the device as soon as no instance is active (or at maxit).
+template <typename T>
+int ensure_loop_graph(pf_plan* p) {
+  if (p->loop_exec) return NRPF_OK;
+  if (!p->capture_stream) CK(cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  auto fail = [&](cudaError_t e) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? NRPF_ERR_NOMEM : NRPF_ERR_CUDA;
+  };
+  cudaGraphConditionalHandle cond = 0;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(e);
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) return fail(e);
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(p->capture_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return fail(e);
+  nrpf::Recorder count;  // launches of one body, by class
+  enqueue_body<T>(p, p->capture_stream, &count, cond, 1);
+  cudaGraph_t captured = nullptr;
+  const cudaError_t el = cudaGetLastError();
+  e = cudaStreamEndCapture(p->capture_stream, &captured);
+  if (el != cudaSuccess) return fail(el);
+  if (e != cudaSuccess) return fail(e);
+  if ((e = cudaGraphInstantiate(&p->loop_exec, g, 0)) != cudaSuccess) {
+    p->loop_exec = nullptr;
+    return fail(e);
+  }
+  p->loop_graph = g;
+  for (int c = 0; c < nrpf::K_NCLASS; ++c) p->body_launches[c] = count.launches[c];
+  return NRPF_OK;
+}
+
+template <typename T>
+int enqueue_solve(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
+                  double* v_out, int32_t* iters, uint8_t* status, cudaStream_t st) {
+  const DevPlan& P = p->dp;
+  const DevState& S = p->st;
   nrpf::Recorder* rec = &p->rec;
   nrpf::launch_load(P, S, B, sbus, v0, st, rec);
-  cudaMemsetAsync(S.n_active, 0, 2 * sizeof(int32_t), st);
-  for (int it = 0; it <= maxit; ++it) {
-    int32_t* counter = S.n_active + (it & 1);
-    const int32_t* prev = it == 0 ? nullptr : S.n_active + ((it - 1) & 1);
-    if (P.m > 0) {
-      nrpf::launch_prepare_lu<T>(P, S, prev, st, rec);
-      nrpf::launch_mismatch<T>(P, S, 1, prev, st, rec);
+  nrpf::launch_ctl_init(S, maxit, tol, st, rec);
+  if (P.m > 0 && maxit > 0) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+      // the caller captures this stream: maxit iterations, instances that
+      // have finished skip through the gates
+      for (int it = 0; it < maxit; ++it) enqueue_body<T>(p, st, rec, 0, 0);
+    } else if (rec->time_mask) {
+      // profiled solve (per-launch events): the host ends the loop
+      for (int it = 0; it < maxit; ++it) {
+        enqueue_body<T>(p, st, rec, 0, 0);
+        CK(cudaMemcpyAsync(p->h_prev, nrpf::ctl_prev(S), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (*p->h_prev == 0) break;
+      }
+    } else {
+      int rc = ensure_loop_graph<T>(p);
+      if (rc) return rc;
+      CK(cudaGraphLaunch(p->loop_exec, st));
     }
-    cudaMemsetAsync(counter, 0, sizeof(int32_t), st);
-    nrpf::launch_check(S, it, maxit, tol, counter, st, rec);
-    if (it == maxit || P.m == 0) break;
-    nrpf::launch_factor<T>(P, S, h.lu_lvl_ptr, counter, st, rec);
-    nrpf::launch_solve<T>(P, S, h.fw_lvl_ptr, h.bw_lvl_ptr, counter, st, rec);
-    nrpf::launch_update<T>(P, S, counter, st, rec);
   }
+  // the last convergence test (iteration ctl->it; nothing is active after an
+  // early exit)
+  if (P.m > 0) {
+    nrpf::launch_prepare_lu<T>(P, S, nrpf::ctl_prev(S), st, rec);
+    nrpf::launch_mismatch<T>(P, S, 1, nrpf::ctl_prev(S), st, rec);
+  }
+  nrpf::launch_check(S, st, rec);
   nrpf::launch_store(P, S, B, v_out, iters, status, st, rec);
+  return NRPF_OK;
 }
 
 int build_pattern_map(pf_plan* p) {
@@ -219,7 +321,7 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
   if (opt) o = *opt;
   // default panel width by precision: FP32 needs the wider panel to feed its
   // FMA pipes with fewer passes over the trailing block
-  if (o.panel == 0) o.panel = o.lu_precision == NRPF_LU_FP32 ? 16 : 8;
+  if (o.panel == 0) o.panel = o.lu_precision == NRPF_LU_FP32 ? 64 : 8;
   // default dense cut by LU precision: an FMA of the sparse phase costs about
   // twice a dense-block FMA in FP64 (the FP64 pipe bounds both) but about 13x
   // in FP32 (the dense block runs at FP32 rate, the sparse phase does not),
@@ -312,6 +414,7 @@ int pf_plan_get_info(const pf_plan* p, pf_plan_info* info) {
   info->solve_fma = h.solve_fma;
   info->capacity = p->capacity;
   info->lu_precision = p->lu_precision;
+  info->panel = h.kb;
   return NRPF_OK;
 }
 
@@ -347,9 +450,10 @@ int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, doub
   if (rc) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (p->lu_precision == NRPF_LU_FP32)
-    enqueue_solve<float>(p, B, sbus, v0, tol, maxit, v_out, iters, status, st);
+    rc = enqueue_solve<float>(p, B, sbus, v0, tol, maxit, v_out, iters, status, st);
   else
-    enqueue_solve<double>(p, B, sbus, v0, tol, maxit, v_out, iters, status, st);
+    rc = enqueue_solve<double>(p, B, sbus, v0, tol, maxit, v_out, iters, status, st);
+  if (rc) return rc;
   return check_launch();
 }
 
@@ -418,6 +522,7 @@ int pf_stage_linear_solve(pf_plan* p, int B, const double* v, const double* rhs,
 
 int pf_profile_start(pf_plan* p, uint32_t time_mask) {
   if (!p || p->host_only) return NRPF_ERR_ARG;
+  fold_graph_launches(p);
   p->rec.reset(time_mask);
   return NRPF_OK;
 }
@@ -425,6 +530,7 @@ int pf_profile_start(pf_plan* p, uint32_t time_mask) {
 int pf_profile_read(pf_plan* p, pf_profile* out) {
   if (!p || !out || p->host_only) return NRPF_ERR_ARG;
   p->rec.drain();
+  fold_graph_launches(p);
   static_assert(nrpf::K_NCLASS <= NRPF_KCLASSES, "kernel class table too small");
   for (int c = 0; c < NRPF_KCLASSES; ++c) {
     out->launches[c] = c < nrpf::K_NCLASS ? p->rec.launches[c] : 0;
@@ -453,6 +559,8 @@ void pf_plan_destroy(pf_plan* p) {
   if (cur != p->device) cudaSetDevice(p->device);
   cudaDeviceSynchronize();
   free_ws(p);
+  if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+  if (p->h_prev) cudaFreeHost(p->h_prev);
   for (void* a : p->plan_allocs) cudaFree(a);
   if (p->d_pattern_map) cudaFree(p->d_pattern_map);
   if (cur != p->device) cudaSetDevice(cur);

@@ -52,6 +52,20 @@ struct DevPlan {
 };
 
 // Per-solve workspace (capacity Bp instances, a multiple of kTile).
+// Device-resident control of the Newton loop, so that one iteration can run
+// unchanged from a graph: every kernel of an iteration reads its gate and the
+// iteration number here.
+struct SolveCtl {
+  int32_t prev;     // instances active after the previous check: gate of the
+                    // LU preparation and mismatch (nonzero before the first)
+  int32_t cur;      // instances active after this iteration's check: gate of
+                    // factorisation, FS/BS and update
+  int32_t it;       // Newton iteration of the check
+  int32_t maxit;
+  double tol;
+  long long graph_iters;  // loop bodies run by the graph since the last reset
+};
+
 struct DevState {
   int Bp;
   double* vm;    // [n] magnitudes
@@ -69,7 +83,7 @@ struct DevState {
   int32_t* status;  // [Bp]
   int32_t* active;  // [Bp]
   int32_t* bad;     // [Bp] non-finite step detected
-  int32_t* n_active;  // [2] active-instance counters (alternating iterations)
+  SolveCtl* ctl;  // Newton loop control (one per workspace)
 };
 
 }  // namespace nrpf

@@ -22,4 +22,12 @@ struct pf_plan {
   int64_t* d_pattern_map = nullptr;  // CCS pattern -> LU element
   int64_t pattern_nnz = 0;
   nrpf::Recorder rec;
+  // Newton loop as a graph: one iteration captured as the body of a WHILE
+  // node whose condition the iteration's last kernel sets (built per
+  // workspace; launches of one body by kernel class, for the counters)
+  cudaGraph_t loop_graph = nullptr;
+  cudaGraphExec_t loop_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  int64_t body_launches[nrpf::K_NCLASS] = {};
+  int32_t* h_prev = nullptr;  // pinned: ctl->prev read back by profiled solves
 };

@@ -222,9 +222,12 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
 
 // Convergence test and per-instance bookkeeping, one thread per instance.
 // it = number of updates performed so far.
-__global__ void k_check(DevState S, int Bp, int it, int maxit, double tol, int32_t* counter) {
+__global__ void k_check(DevState S, int Bp) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= Bp) return;
+  const int it = S.ctl->it, maxit = S.ctl->maxit;
+  const double tol = S.ctl->tol;
+  int32_t* counter = &S.ctl->cur;
   const double nrm = __longlong_as_double((long long)S.norm[b]);
   S.norm[b] = 0ull;
   if (!S.active[b]) return;
@@ -248,6 +251,27 @@ __global__ void k_check(DevState S, int Bp, int it, int maxit, double tol, int32
   S.active[b] = keep;
   const unsigned mask = __ballot_sync(__activemask(), keep);
   if (keep && (threadIdx.x & 31) == __ffs(mask) - 1) atomicAdd(counter, __popc(mask));
+}
+
+__global__ void k_ctl_init(SolveCtl* c, int maxit, double tol) {
+  c->prev = 1;
+  c->cur = 0;
+  c->it = 0;
+  c->maxit = maxit;
+  c->tol = tol;
+}
+
+// One thread.  The check of this iteration has finished (stream order), so
+// cur is final.
+__global__ void k_iter_tail(SolveCtl* c, cudaGraphConditionalHandle cond, int graph) {
+  const int cur = c->cur;
+  c->prev = cur;
+  c->cur = 0;
+  c->it += 1;
+  if (graph) {
+    c->graph_iters += 1;
+    cudaGraphSetConditional(cond, (cur > 0 && c->it < c->maxit) ? 1u : 0u);
+  }
 }
 
 // Zero a buffer (16-byte stores, grid-stride), skipped once no instance is
@@ -369,44 +393,90 @@ __global__ void k_dense_diag(DevPlan P, DevState S, int k, const int32_t* __rest
     for (int r = 0; r < KB; ++r) A[dense_off<T>(k + r, k + c, ld, lane)] = D[r][c];
 }
 
+// four consecutive rows r .. r+3 (r a multiple of 4) of dense column c for
+// this lane: one 16-byte load in the grouped FP32 layout, four loads in FP64
+template <typename T>
+__device__ __forceinline__ void ld4(const T* __restrict__ A, int r, int c, int ld, int lane, T (&v)[4]) {
+  if constexpr (DenseGroup<T>::G == 4) {
+    const float4 q = reinterpret_cast<const float4*>(A)[((size_t)c * ld + r) * 8 + lane];
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = A[dense_off<T>(r + i, c, ld, lane)];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* __restrict__ A, int r, int c, int ld, int lane, const T (&v)[4]) {
+  if constexpr (DenseGroup<T>::G == 4) {
+    reinterpret_cast<float4*>(A)[((size_t)c * ld + r) * 8 + lane] = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) A[dense_off<T>(r + i, c, ld, lane)] = v[i];
+  }
+}
+
+// y <- L^-1 y for NC columns held in registers, L the NR x NR unit-lower
+// block at dense (k, k): column-oriented forward elimination, the
+// subtractions into each y[c] in ascending p
+template <typename T, int NR, int NC>
+__device__ __forceinline__ void unit_lower_solve(const T* __restrict__ A, int k, int ld, int lane, T (&y)[NC][NR]) {
+#pragma unroll
+  for (int p = 0; p < NR - 1; ++p)
+#pragma unroll
+    for (int q = (p + 1) / 4; q < NR / 4; ++q) {
+      T l[4];
+      ld4(A, k + 4 * q, k + p, ld, lane, l);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (4 * q + i > p) {
+#pragma unroll
+          for (int t = 0; t < NC; ++t) y[t][4 * q + i] -= l[i] * y[t][p];
+        }
+    }
+}
+
 template <typename T, int KB>
-__global__ void k_dense_panel(DevPlan P, DevState S, int k, const int32_t* __restrict__ gate) {
+__global__ void k_dense_panel(DevPlan P, DevState S, int k, int cend, const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;
   const int lane = threadIdx.x;
   const int tile = blockIdx.y;
   if (!tile_active(S, tile, lane)) return;
   const int ld = P.ndp;
-  const int r0 = k + KB;            // first trailing row/column
-  const int ngrp = (ld - r0) / 4;   // groups of four rows (and of four columns)
+  const int r0 = k + KB;              // first trailing row/column
+  const int ngrp = (ld - r0) / 4;     // groups of four rows (down to ld)
+  const int ngc = (cend - r0) / 4;    // groups of four columns (up to cend)
   const int g = blockIdx.x * blockDim.y + threadIdx.y;
-  if (g >= 2 * ngrp) return;
+  if (g >= ngrp + ngc) return;
   T* __restrict__ A = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile;  // dense block
   const T* __restrict__ inv = reinterpret_cast<const T*>(S.inv) + (size_t)tile * KB * kTile + lane;
-  auto at = [&](int r, int c) -> T& { return A[dense_off<T>(r, c, ld, lane)]; };
   if (g < ngrp) {
-    // rows i0..i0+3: x U11 = a  (U11 upper, pivots inverted)
+    // rows i0..i0+3: x U11 = a  (U11 upper, pivots inverted), column by
+    // column; the subtractions into x[c] in ascending p
     const int i0 = r0 + 4 * g;
-    T x[4][KB];
+    T x[KB][4];
 #pragma unroll
-    for (int c = 0; c < KB; ++c)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) x[t][c] = at(i0 + t, k + c);
+    for (int c = 0; c < KB; ++c) ld4(A, i0, k + c, ld, lane, x[c]);
 #pragma unroll
     for (int c = 0; c < KB; ++c) {
 #pragma unroll
-      for (int p = 0; p < c; ++p) {
-        const T u = at(k + p, k + c);
+      for (int q = 0; q < KB / 4; ++q) {
+        if (4 * q >= c) break;
+        T u[4];
+        ld4(A, k + 4 * q, k + c, ld, lane, u);  // U(k+4q .. k+4q+3, k+c)
 #pragma unroll
-        for (int t = 0; t < 4; ++t) x[t][c] -= x[t][p] * u;
+        for (int i = 0; i < 4; ++i)
+          if (4 * q + i < c) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) x[c][t] -= x[4 * q + i][t] * u[i];
+          }
       }
       const T ip = inv[c * kTile];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) x[t][c] *= ip;
+      for (int t = 0; t < 4; ++t) x[c][t] *= ip;
     }
 #pragma unroll
-    for (int c = 0; c < KB; ++c)
-#pragma unroll
-      for (int t = 0; t < 4; ++t) at(i0 + t, k + c) = x[t][c];
+    for (int c = 0; c < KB; ++c) st4(A, i0, k + c, ld, lane, x[c]);
   } else {
     // columns j0..j0+3: L11 y = a  (L11 unit lower)
     const int j0 = r0 + 4 * (g - ngrp);
@@ -414,19 +484,20 @@ __global__ void k_dense_panel(DevPlan P, DevState S, int k, const int32_t* __res
 #pragma unroll
     for (int t = 0; t < 4; ++t)
 #pragma unroll
-      for (int c = 0; c < KB; ++c) y[t][c] = at(k + c, j0 + t);
+      for (int q = 0; q < KB / 4; ++q) {
+        T v[4];
+        ld4(A, k + 4 * q, j0 + t, ld, lane, v);
 #pragma unroll
-    for (int c = 1; c < KB; ++c)
-#pragma unroll
-      for (int p = 0; p < c; ++p) {
-        const T l = at(k + c, k + p);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) y[t][c] -= l * y[t][p];
+        for (int i = 0; i < 4; ++i) y[t][4 * q + i] = v[i];
       }
+    unit_lower_solve<T, KB, 4>(A, k, ld, lane, y);
 #pragma unroll
     for (int t = 0; t < 4; ++t)
 #pragma unroll
-      for (int c = 0; c < KB; ++c) at(k + c, j0 + t) = y[t][c];
+      for (int q = 0; q < KB / 4; ++q) {
+        const T v[4] = {y[t][4 * q], y[t][4 * q + 1], y[t][4 * q + 2], y[t][4 * q + 3]};
+        st4(A, k + 4 * q, j0 + t, ld, lane, v);
+      }
   }
 }
 
@@ -437,20 +508,31 @@ struct UpdOcc {
   static constexpr int value = (sizeof(T) == 4 && TS == 8) ? 3 : 6;
 };
 
+// The updated region is the trailing block [r0, ld) x [r0, ld) without its
+// part [kend, ld) x [kend, ld): kend = ld for a one-level panel (the whole
+// trailing block); kend = the end of the outer panel for an inner step of a
+// two-level panel (the outer panel's own columns, and its rows to the right).
 template <typename T, int KB, int TS>
-__global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevPlan P, DevState S, int k,
-                                                                           const int32_t* __restrict__ gate) {
+__global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevPlan P, DevState S, int k, int kend,
+                                                                           int cend, const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;
   const int lane = threadIdx.x;
   const int tile = blockIdx.y;
   if (!tile_active(S, tile, lane)) return;
   const int ld = P.ndp;
   const int r0 = k + KB;
-  const int nb = (ld - r0) / TS;
+  const int nbr = (ld - r0) / TS, nbk = (kend - r0) / TS, nbx = (cend - kend) / TS;
+  const int n1 = nbr * nbk;  // columns [r0, kend), all rows
   const int t = blockIdx.x * blockDim.y + threadIdx.y;
-  if (t >= nb * nb) return;
-  const int bi = t % nb, bj = t / nb;
-  const int i0 = r0 + TS * bi, j0 = r0 + TS * bj;
+  if (t >= n1 + nbk * nbx) return;
+  int i0, j0;
+  if (t < n1) {
+    i0 = r0 + TS * (t % nbr);
+    j0 = r0 + TS * (t / nbr);
+  } else {  // rows [r0, kend), columns [kend, ld)
+    i0 = r0 + TS * ((t - n1) % nbk);
+    j0 = kend + TS * ((t - n1) / nbk);
+  }
   T* __restrict__ Ab = reinterpret_cast<T*>(S.lu) + ((size_t)tile * P.NLU + P.NS) * kTile;  // dense block
   T acc[TS][TS];
   if constexpr (DenseGroup<T>::G == 4 && TS == 8) {
@@ -467,7 +549,7 @@ __global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevP
         acc[4 * h + 2][c] = v.z;
         acc[4 * h + 3][c] = v.w;
       }
-#pragma unroll
+#pragma unroll(KB > 16 ? 2 : KB / 4)
     for (int pp = 0; pp < KB / 4; ++pp) {
       float4 bq[TS];  // rows k+4pp .. k+4pp+3 of columns j0 .. j0+7 (U12)
 #pragma unroll
@@ -504,7 +586,7 @@ __global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevP
     for (int c = 0; c < TS; ++c)
 #pragma unroll
       for (int r = 0; r < TS; ++r) acc[r][c] = cj[c * cstride + r * kTile];
-#pragma unroll
+#pragma unroll(KB > 16 ? 8 : KB)
     for (int p = 0; p < KB; ++p) {
       T a[TS], b[TS];
 #pragma unroll
@@ -526,7 +608,7 @@ __global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevP
     for (int c = 0; c < TS; ++c)
 #pragma unroll
       for (int r = 0; r < TS; ++r) acc[r][c] = Ab[dense_off<T>(i0 + r, j0 + c, ld, lane)];
-#pragma unroll
+#pragma unroll(KB > 16 ? 8 : KB)
     for (int p = 0; p < KB; ++p) {
       T a[TS], b[TS];
 #pragma unroll
@@ -786,10 +868,17 @@ void launch_mismatch(const DevPlan& P, const DevState& S, int jac, const int32_t
   NRPF_LAUNCH(rec, K_MISMATCH, st, k_mismatch_jac<T><<<g, dim3(32, kMWarps), 0, st>>>(P, S, jac, gate));
 }
 
-void launch_check(const DevState& S, int it, int maxit, double tol, int32_t* counter, cudaStream_t st,
-                  Recorder* rec) {
-  NRPF_LAUNCH(rec, K_CHECK, st,
-              k_check<<<(S.Bp + 255) / 256, 256, 0, st>>>(S, S.Bp, it, maxit, tol, counter));
+void launch_ctl_init(const DevState& S, int maxit, double tol, cudaStream_t st, Recorder* rec) {
+  NRPF_LAUNCH(rec, K_AUX, st, k_ctl_init<<<1, 1, 0, st>>>(S.ctl, maxit, tol));
+}
+
+void launch_check(const DevState& S, cudaStream_t st, Recorder* rec) {
+  NRPF_LAUNCH(rec, K_CHECK, st, k_check<<<(S.Bp + 255) / 256, 256, 0, st>>>(S, S.Bp));
+}
+
+void launch_iter_tail(const DevState& S, cudaGraphConditionalHandle cond, int graph, cudaStream_t st,
+                      Recorder* rec) {
+  NRPF_LAUNCH(rec, K_AUX, st, k_iter_tail<<<1, 1, 0, st>>>(S.ctl, cond, graph));
 }
 
 template <typename T>
@@ -804,22 +893,50 @@ void launch_prepare_lu(const DevPlan& P, const DevState& S, const int32_t* gate,
     NRPF_LAUNCH(rec, K_ONES, st, k_set_ones<T><<<dim3(1, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate));
 }
 
+// one panel step of width KB at column k.  The column part of the panel
+// covers columns < cend; the update covers the trailing block's columns
+// [r0, kend) and, for rows [r0, kend), columns [kend, cend)
+// (kend = cend = ld: the whole trailing block).
 template <typename T, int KB>
-static void launch_dense_step(const DevPlan& P, const DevState& S, int k, const int32_t* gate, cudaStream_t st,
-                              Recorder* rec) {
+static void launch_dense_step(const DevPlan& P, const DevState& S, int k, int kend, int cend, const int32_t* gate,
+                              cudaStream_t st, Recorder* rec) {
   const int tiles = S.Bp / kTile;
-  const int rem = P.ndp - k - KB;
+  const int rows = P.ndp - k - KB;
   NRPF_LAUNCH(rec, K_DENSE_DIAG, st,
               k_dense_diag<T, KB><<<(tiles + 3) / 4, dim3(32, 4), 0, st>>>(P, S, k, gate));
-  if (rem > 0) {
+  if (rows > 0) {
+    const int cols = cend - k - KB;
     NRPF_LAUNCH(rec, K_DENSE_PANEL, st,
-                k_dense_panel<T, KB><<<grid2(2 * (rem / 4), 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, gate));
+                k_dense_panel<T, KB><<<grid2(rows / 4 + cols / 4, 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, cend,
+                                                                                                  gate));
     // register tile: 4 x 4 for FP64 (the FP64 pipe is the bound), 8 x 8 for
     // FP32 (halves the loads per multiply-add; FP32 is load-bound)
     constexpr int TS = (sizeof(T) == 4 && KB >= 8) ? 8 : 4;
+    const int64_t nk = (kend - k - KB) / TS;
+    const int64_t ntiles = (rows / TS) * nk + nk * ((cend - kend) / TS);
+    if (ntiles > 0) {
+      NRPF_LAUNCH(rec, K_DENSE_UPDATE, st,
+                  k_dense_update<T, KB, TS><<<grid2(ntiles, 4, tiles), dim3(32, 4), 0, st>>>(P, S, k, kend, cend,
+                                                                                            gate));
+    }
+  }
+}
+
+// Outer panel of width KBO (two-level blocking): 16-wide steps factorise the
+// outer panel's columns and its rows to the right (U12), each step updating
+// only that L-shaped region; then one trailing update of depth KBO (one pass
+// over the trailing block per KBO columns instead of per 16).
+template <typename T, int KBO>
+static void launch_dense_outer(const DevPlan& P, const DevState& S, int k, const int32_t* gate, cudaStream_t st,
+                               Recorder* rec) {
+  const int tiles = S.Bp / kTile;
+  for (int ki = k; ki < k + KBO; ki += 16) launch_dense_step<T, 16>(P, S, ki, k + KBO, P.ndp, gate, st, rec);
+  const int rest = P.ndp - k - KBO;
+  if (rest > 0) {
+    constexpr int TS = sizeof(T) == 4 ? 8 : 4;
     NRPF_LAUNCH(rec, K_DENSE_UPDATE, st,
-                k_dense_update<T, KB, TS><<<grid2((int64_t)(rem / TS) * (rem / TS), 4, tiles), dim3(32, 4), 0, st>>>(
-                    P, S, k, gate));
+                k_dense_update<T, KBO, TS><<<grid2((int64_t)(rest / TS) * (rest / TS), 4, tiles), dim3(32, 4), 0,
+                                             st>>>(P, S, k, P.ndp, P.ndp, gate));
   }
 }
 
@@ -835,9 +952,11 @@ void launch_factor(const DevPlan& P, const DevState& S, const std::vector<int32_
                                                                                                   gate));
   }
   for (int k = 0; k < P.ndp; k += P.kb) {
-    if (P.kb == 4) launch_dense_step<T, 4>(P, S, k, gate, st, rec);
-    else if (P.kb == 8) launch_dense_step<T, 8>(P, S, k, gate, st, rec);
-    else launch_dense_step<T, 16>(P, S, k, gate, st, rec);
+    if (P.kb == 4) launch_dense_step<T, 4>(P, S, k, P.ndp, P.ndp, gate, st, rec);
+    else if (P.kb == 8) launch_dense_step<T, 8>(P, S, k, P.ndp, P.ndp, gate, st, rec);
+    else if (P.kb == 16) launch_dense_step<T, 16>(P, S, k, P.ndp, P.ndp, gate, st, rec);
+    else if (P.kb == 32) launch_dense_outer<T, 32>(P, S, k, gate, st, rec);
+    else launch_dense_outer<T, 64>(P, S, k, gate, st, rec);
   }
 }
 

@@ -1,5 +1,6 @@
 // Launchers of the batched Newton-Raphson kernels (kernels.cu).
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <vector>
 
@@ -18,8 +19,24 @@ void launch_load(const DevPlan& P, const DevState& S, int B, const double* sbus,
                  cudaStream_t st, Recorder* rec = nullptr);
 void launch_store(const DevPlan& P, const DevState& S, int B, double* v_out, int32_t* iters,
                   uint8_t* status, cudaStream_t st, Recorder* rec = nullptr);
-void launch_check(const DevState& S, int it, int maxit, double tol, int32_t* counter, cudaStream_t st,
-                  Recorder* rec = nullptr);
+// gates of the Newton loop (addresses inside the device control block)
+inline const int32_t* ctl_prev(const DevState& S) {
+  return reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(S.ctl) + offsetof(SolveCtl, prev));
+}
+inline const int32_t* ctl_cur(const DevState& S) {
+  return reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(S.ctl) + offsetof(SolveCtl, cur));
+}
+
+// Reset the loop control (prev = 1, cur = 0, it = 0) with the tolerance and
+// iteration limit of this solve.
+void launch_ctl_init(const DevState& S, int maxit, double tol, cudaStream_t st, Recorder* rec = nullptr);
+// Convergence test of iteration ctl->it: counts the instances still active
+// into ctl->cur.
+void launch_check(const DevState& S, cudaStream_t st, Recorder* rec = nullptr);
+// End of one iteration: prev = cur, cur = 0, it += 1; with a graph handle
+// (graph != 0), also sets the loop's condition to (cur > 0 && it < maxit).
+void launch_iter_tail(const DevState& S, cudaGraphConditionalHandle cond, int graph, cudaStream_t st,
+                      Recorder* rec = nullptr);
 
 template <typename T>
 void launch_mismatch(const DevPlan& P, const DevState& S, int jac, const int32_t* gate, cudaStream_t st,

@@ -67,7 +67,10 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
                HostPlan& P, std::string& err) {
   int rc = validate(n, rowptr, colidx, yre, yim, bt, err);
   if (rc) return rc;
-  if (kb != 4 && kb != 8 && kb != 16) { err = "panel must be 4, 8 or 16"; return NRPF_ERR_ARG; }
+  if (kb != 4 && kb != 8 && kb != 16 && kb != 32 && kb != 64) {
+    err = "panel must be 4, 8, 16, 32 or 64";
+    return NRPF_ERR_ARG;
+  }
   const int nnzY = rowptr[n];
   P.n = n;
   P.kb = kb;

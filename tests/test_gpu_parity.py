@@ -79,7 +79,10 @@ def test_mismatch_stage(name, B):
                                        ("mesh2000_b10k", 3, {}),
                                        ("mesh30_b64", 40, {"lu_precision": "fp32"}),
                                        ("mesh30_b64", 35, {"lu_precision": "fp32", "panel": 8}),
-                                       ("mesh2000_b10k", 3, {"lu_precision": "fp32"})])
+                                       ("mesh2000_b10k", 3, {"lu_precision": "fp32"}),
+                                       ("mesh30_b64", 36, {"panel": 32}),
+                                       ("mesh2000_b10k", 3, {"lu_precision": "fp32", "panel": 32}),
+                                       ("mesh2000_b10k", 2, {"lu_precision": "fp32", "panel": 64})])
 def test_jacobian_and_factor_stage(name, B, kw):
     g, S, V0 = case(name, batch=B)
     V = perturbed(V0, seed=4)
@@ -108,7 +111,11 @@ def test_jacobian_and_factor_stage(name, B, kw):
 @pytest.mark.parametrize("name,B,kw", [("mesh30_b64", 64, {}), ("mesh30_b64", 70, {"panel": 4}),
                                        ("mesh30_b64", 32, {"panel": 16}), ("mesh2000_b10k", 8, {}),
                                        ("mesh30_b64", 64, {"lu_precision": "fp32"}),
-                                       ("mesh2000_b10k", 8, {"lu_precision": "fp32"})])
+                                       ("mesh2000_b10k", 8, {"lu_precision": "fp32"}),
+                                       ("mesh30_b64", 40, {"lu_precision": "fp32", "panel": 32}),
+                                       ("mesh2000_b10k", 8, {"lu_precision": "fp32", "panel": 32}),
+                                       ("mesh30_b64", 33, {"panel": 64}),
+                                       ("mesh2000_b10k", 8, {"lu_precision": "fp32", "panel": 64})])
 def test_linear_solve_stage(name, B, kw):
     g, S, V0 = case(name, batch=B)
     V = perturbed(V0, seed=5)
@@ -212,12 +219,14 @@ def test_plan_reuse_and_capacity_growth():
         assert p.info["capacity"] >= 64
 
 
-@pytest.mark.parametrize("name,B", [("mesh30_b64", 64), ("mesh2000_b10k", 40)])
-def test_mixed_precision_lu(name, B):
+@pytest.mark.parametrize("name,B,panel", [("mesh30_b64", 64, 0), ("mesh2000_b10k", 40, 0),
+                                          ("mesh2000_b10k", 40, 32), ("mesh2000_b10k", 40, 64)])
+def test_mixed_precision_lu(name, B, panel):
     """FP32 LU + FS/BS, FP64 mismatch/update: same statuses, same tolerance,
-    a few more iterations at most."""
+    a few more iterations at most (default panel, and the two-level panels of
+    32 and 64 factorised in steps of 16)."""
     g, S, V0 = case(name, batch=B)
-    with _plan(g, lu_precision="fp32") as p:
+    with _plan(g, lu_precision="fp32", panel=panel) as p:
         v, it, st = p.solve(_dev(S), _dev(V0), TOL, 20)
         Vg, itg, stg = v.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
     idx = list(range(0, B, max(1, B // 10)))
@@ -240,3 +249,38 @@ def test_fresh_workspace_ignores_stale_memory():
         with _plan(g) as p:
             v, it, st = p.solve(_dev(S), _dev(V0), TOL, 10)
             assert np.all(st.cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("lu,maxit", [("fp64", 10), ("fp32", 10), ("fp64", 2)])
+def test_loop_graph_matches_host_loops(lu, maxit):
+    """The Newton loop run as a graph WHILE node (default), as a host loop
+    ended from the host (profiled solves) and as a fixed-count loop inside a
+    caller's stream capture give identical results; the graph runs one body
+    per check up to the last active instance's, not maxit."""
+    g, S, V0 = case("mesh30_b64", batch=64)
+    Sd, Vd = _dev(S), _dev(V0)
+    with _plan(g, lu_precision=lu) as p:
+        outs = [tuple(torch.empty_like(t) for t in p.solve(Sd, Vd, TOL, maxit)) for _ in range(3)]
+        p.profile_start([])
+        p.solve(Sd, Vd, TOL, maxit, out=outs[0])
+        counts = p.profile_read()
+        p.profile_start(["dense_update"])
+        p.solve(Sd, Vd, TOL, maxit, out=outs[1])
+        p.profile_read()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            p.solve(Sd, Vd, TOL, maxit, out=outs[2])
+        graph.replay()
+        torch.cuda.synchronize()
+    a, b, c = outs
+    for x, y in ((a, b), (a, c)):
+        assert torch.equal(x[0], y[0]) and torch.equal(x[1], y[1]) and torch.equal(x[2], y[2])
+    st, it = a[2].cpu().numpy(), a[1].cpu().numpy()
+    if maxit == 10:
+        assert np.all(st == 0)
+        bodies = int(it.max()) + 1  # the check that finds no instance active ends the loop
+    else:
+        assert np.all(st == 1) and np.all(it == maxit)
+        bodies = maxit
+    assert counts["check"][0] == bodies + 1  # plus the final test after the loop
+    assert counts["update"][0] == bodies

@@ -87,9 +87,9 @@ def test_plan_pattern_mesh30_amd_and_natural():
     d = _check_pattern(g, _plan(g, dense_frac=1.0))
     assert d["dense_dim"] == 0 and n["dense_dim"] == 0
     assert a["dense_dim"] > 0 and a["sparse_cols"] + a["dense_dim"] == a["m"]
-    for kb in (4, 8, 16):
+    for kb in (4, 8, 16, 32, 64):
         i = _plan(g, panel=kb).info
-        assert i["dense_pad"] % kb == 0 and i["dense_pad"] >= i["dense_dim"]
+        assert i["dense_pad"] % kb == 0 and i["dense_pad"] >= i["dense_dim"] and i["panel"] == kb
 
 
 def test_plan_tree_has_no_fill():
