@@ -216,41 +216,49 @@ def combine_ranks(ms, converged, device):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+# ncu DRAM bytes over algorithmic bytes of the depth-64 FP32 trailing update
+# (373.2 MB of 419.4 MB, profiles/dense_update_fp32_mesh2000.md).
+DENSE_UPDATE_FP32_DRAM_PER_ALG = 373.2 / 419.4
+
 KERNEL_TIMING = ("CUDA events around every dense_update launch on its stream, during a second pass of the "
                  "K timed steps")
 
 
-def dense_update_blocks(ndp, kb):
-    """The rectangular updates A[rows, cols] -= L U of depth `depth` that one
-    dense refactor launches, as (rows, cols, depth): one trailing update per
-    panel for panels of 4-16; for the two-level panels (32, 64) the updates of
-    the 16-wide inner steps limited to the outer panel's columns, then one
-    trailing update of depth 32 / 64 per outer panel."""
+def dense_update_launches(ndp, kb):
+    """The k_dense_update launches of one dense refactor, each a list of the
+    rectangles A[rows, cols] -= L U of depth d it updates, as (rows, cols, d).
+    Panels of 4-16: one trailing update per panel.  Two-level panels (32, 64):
+    per 16-wide inner step, the outer panel's columns below the step plus, for
+    the outer panel's rows below the step, the columns right of the outer panel
+    (one L-shaped launch); then one trailing update of depth kb per outer
+    panel."""
     out = []
     for k in range(0, ndp, kb):
         if kb <= 16:
             if ndp - k - kb > 0:
-                out.append((ndp - k - kb, ndp - k - kb, kb))
+                out.append([(ndp - k - kb, ndp - k - kb, kb)])
             continue
         for ki in range(k, k + kb, 16):
-            rows, cols = ndp - ki - 16, k + kb - ki - 16
-            if rows > 0 and cols > 0:
-                out.append((rows, cols, 16))
+            r0, kend = ki + 16, k + kb
+            rects = [(ndp - r0, kend - r0, 16), (kend - r0, ndp - kend, 16)]
+            rects = [r for r in rects if r[0] > 0 and r[1] > 0]
+            if rects:
+                out.append(rects)
         if ndp - k - kb > 0:
-            out.append((ndp - k - kb, ndp - k - kb, kb))
+            out.append([(ndp - k - kb, ndp - k - kb, kb)])
     return out
 
 
 def dense_update_flop(ndp, kb):
-    """Algorithmic flops of the rectangular updates of one dense refactor:
-    2 * rows * cols * depth each."""
-    return sum(2 * r * c * d for r, c, d in dense_update_blocks(ndp, kb))
+    """Algorithmic flops of the updates of one dense refactor: 2 * rows * cols
+    * depth per rectangle."""
+    return sum(2 * r * c * d for L in dense_update_launches(ndp, kb) for r, c, d in L)
 
 
 def dense_update_bytes(ndp, kb, w):
-    """Algorithmic bytes of the same updates: the updated block read and
-    written once, the two operand panels read once (w bytes a value)."""
-    return sum(w * (2 * r * c + d * (r + c)) for r, c, d in dense_update_blocks(ndp, kb))
+    """Algorithmic bytes of the same updates: each rectangle read and written
+    once, its two operand panels read once (w bytes a value)."""
+    return sum(w * (2 * r * c + d * (r + c)) for L in dense_update_launches(ndp, kb) for r, c, d in L)
 
 
 def run_feeders(args):
@@ -635,6 +643,9 @@ def run_ours(args):
     # algorithmic bytes of the trailing updates: the trailing block read and
     # written once per panel, plus the two panels, per refactor
     du_bytes = dense_update_bytes(ndp, kb, w) * refactors
+    # launches that update something: one set per batch refactor (the body
+    # whose check finds no instance active launches gated no-ops)
+    active_launches = len(dense_update_launches(ndp, kb)) * int(iters.max()) * args.steps
     r2 = [(ndp - k - kb) ** 2 for k in range(0, ndp, kb) if ndp - k - kb > 0]
     traffic = (DENSE_UPDATE_DRAM_B_PER_R2 * B * sum(r2) / len(r2)
                if r2 and args.lu == "fp64" and kb == 8 else None)
@@ -669,7 +680,10 @@ def run_ours(args):
                      {"bound": "hbm", "kernel": "dense_update",
                       "achieved": du_bytes / (du[2] / 1e3) / 1e9 if du[2] > 0 else None, "peak": hbm,
                       "unit": "GB/s", "frac": (du_bytes / (du[2] / 1e3) / 1e9 / hbm) if du[2] > 0 else None,
-                      "traffic": None, "peak_kind": f"{hbm_kind} HBM copy bandwidth",
+                      "traffic": DENSE_UPDATE_FP32_DRAM_PER_ALG * du_bytes / active_launches,
+                      "traffic_kind": "ncu DRAM bytes / algorithmic bytes of a batch-640 depth-64 capture, times the "
+                                      "algorithmic bytes per launch",
+                      "peak_kind": f"{hbm_kind} HBM copy bandwidth",
                       "fp32_tflops": achieved, "fp32_peak_tflops": fp32_peak,
                       "launches": du[0], "ms_total": du[2], "timing": KERNEL_TIMING}),
         "hbm_roofline": {"algorithmic_bytes_per_instance_iteration": bmin,
