@@ -146,6 +146,30 @@ int pf_plan_get_pattern(const pf_plan* p, int32_t* pos_of_unknown, int64_t* colp
 int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
                    double* v_out, int32_t* iters, uint8_t* status, void* stream);
 
+/* pf_solve_batch for a batch held in host memory (the paper's stream study,
+ * Sec. 3.2 / Sec. 5: copies overlapped with computation).  The batch is cut
+ * into chunks of `chunk` instances (0 = the whole batch).  Each chunk goes
+ * through one of two device staging slots owned by the plan, used in turn
+ * across chunks and across calls: its inputs are copied in on a copy-in
+ * stream owned by the plan, it is solved on `stream`, and its results are
+ * copied out on a copy-out stream owned by the plan.  A copy-in waits only
+ * for its slot to be free (the copy-out of the chunk that used it before),
+ * so it overlaps the solve of the previous chunk or of the previous call.
+ * host in : sbus [B,n], v0 [B,n] complex (page-locked memory lets the copies
+ *           run asynchronously; pageable memory works but serialises them).
+ *           They are read at some time after the call: do not modify them
+ *           until `stream` has completed the call's work.
+ * host out: v_out [B,n] complex, iters [B], status [B] (as pf_solve_batch).
+ * stream  : the caller's stream; the solves are ordered after the work
+ *           already on it, and work enqueued on it later runs after the last
+ *           result has reached host memory.  Asynchronous: synchronise
+ *           `stream` before reading the outputs.
+ * The workspace is sized for one chunk (grown as in pf_solve_batch); the
+ * staging slots grow (synchronously) when a larger chunk is asked for.
+ * Errors: as pf_solve_batch; NRPF_ERR_ARG also for chunk < 0. */
+int pf_solve_batch_host(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
+                        double* v_out, int32_t* iters, uint8_t* status, int chunk, void* stream);
+
 /* ---- single stages, for tests and profiling (same layouts as above) ---- */
 
 /* Alg. 1 at voltages v: F [B,m] float64 in J row order (dP of the PV buses,

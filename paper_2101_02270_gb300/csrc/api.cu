@@ -57,16 +57,17 @@ void fold_graph_launches(pf_plan* p) {
   cudaMemcpy(f, &zero, sizeof(zero), cudaMemcpyHostToDevice);
 }
 
-void destroy_loop_graph(pf_plan* p) {
-  if (p->loop_exec) cudaGraphExecDestroy(p->loop_exec);
-  if (p->loop_graph) cudaGraphDestroy(p->loop_graph);
-  p->loop_exec = nullptr;
-  p->loop_graph = nullptr;
+void destroy_loop_graphs(pf_plan* p) {
+  for (auto& kv : p->loops) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  p->loops.clear();
 }
 
 void free_ws(pf_plan* p) {
   fold_graph_launches(p);
-  destroy_loop_graph(p);
+  destroy_loop_graphs(p);
   for (void* a : p->ws_allocs) cudaFree(a);
   p->ws_allocs.clear();
   p->capacity = 0;
@@ -125,9 +126,9 @@ int ensure_capacity(pf_plan* p, int B) {
 // refactorisation, FS/BS and update (gated by this check), and the tail that
 // advances the loop control.
 template <typename T>
-void enqueue_body(pf_plan* p, cudaStream_t st, nrpf::Recorder* rec, cudaGraphConditionalHandle cond, int graph) {
+void enqueue_body(pf_plan* p, const DevState& S, cudaStream_t st, nrpf::Recorder* rec,
+                  cudaGraphConditionalHandle cond, int graph) {
   const DevPlan& P = p->dp;
-  const DevState& S = p->st;
   const HostPlan& h = p->hp;
   const int32_t* prev = nrpf::ctl_prev(S);
   const int32_t* cur = nrpf::ctl_cur(S);
@@ -141,11 +142,16 @@ void enqueue_body(pf_plan* p, cudaStream_t st, nrpf::Recorder* rec, cudaGraphCon
 }
 
 // The loop graph: a WHILE node whose body is one iteration, captured once per
-// workspace; the iteration's tail kernel sets the condition, so the loop ends
-// on the device as soon as no instance is active (or at maxit).
+// workspace and padded batch size; the iteration's tail kernel sets the
+// condition, so the loop ends on the device as soon as no instance is active
+// (or at maxit).
 template <typename T>
-int ensure_loop_graph(pf_plan* p) {
-  if (p->loop_exec) return NRPF_OK;
+int ensure_loop_graph(pf_plan* p, const DevState& S, cudaGraphExec_t* out) {
+  auto it = p->loops.find(S.Bp);
+  if (it != p->loops.end()) {
+    *out = it->second.exec;
+    return NRPF_OK;
+  }
   if (!p->capture_stream) CK(cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
@@ -168,18 +174,17 @@ int ensure_loop_graph(pf_plan* p) {
   e = cudaStreamBeginCaptureToGraph(p->capture_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return fail(e);
   nrpf::Recorder count;  // launches of one body, by class
-  enqueue_body<T>(p, p->capture_stream, &count, cond, 1);
+  enqueue_body<T>(p, S, p->capture_stream, &count, cond, 1);
   cudaGraph_t captured = nullptr;
   const cudaError_t el = cudaGetLastError();
   e = cudaStreamEndCapture(p->capture_stream, &captured);
   if (el != cudaSuccess) return fail(el);
   if (e != cudaSuccess) return fail(e);
-  if ((e = cudaGraphInstantiate(&p->loop_exec, g, 0)) != cudaSuccess) {
-    p->loop_exec = nullptr;
-    return fail(e);
-  }
-  p->loop_graph = g;
+  cudaGraphExec_t exec = nullptr;
+  if ((e = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess) return fail(e);
+  p->loops[S.Bp] = pf_plan::LoopGraph{g, exec};
   for (int c = 0; c < nrpf::K_NCLASS; ++c) p->body_launches[c] = count.launches[c];
+  *out = exec;
   return NRPF_OK;
 }
 
@@ -187,7 +192,10 @@ template <typename T>
 int enqueue_solve(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
                   double* v_out, int32_t* iters, uint8_t* status, cudaStream_t st) {
   const DevPlan& P = p->dp;
-  const DevState& S = p->st;
+  // grids cover this batch's tiles only (tiles are contiguous per array, so
+  // the first Bp of the workspace's capacity serve)
+  DevState S = p->st;
+  S.Bp = (B + kTile - 1) / kTile * kTile;
   nrpf::Recorder* rec = &p->rec;
   nrpf::launch_load(P, S, B, sbus, v0, st, rec);
   nrpf::launch_ctl_init(S, maxit, tol, st, rec);
@@ -197,19 +205,20 @@ int enqueue_solve(pf_plan* p, int B, const double* sbus, const double* v0, doubl
     if (cs != cudaStreamCaptureStatusNone) {
       // the caller captures this stream: maxit iterations, instances that
       // have finished skip through the gates
-      for (int it = 0; it < maxit; ++it) enqueue_body<T>(p, st, rec, 0, 0);
+      for (int it = 0; it < maxit; ++it) enqueue_body<T>(p, S, st, rec, 0, 0);
     } else if (rec->time_mask) {
       // profiled solve (per-launch events): the host ends the loop
       for (int it = 0; it < maxit; ++it) {
-        enqueue_body<T>(p, st, rec, 0, 0);
+        enqueue_body<T>(p, S, st, rec, 0, 0);
         CK(cudaMemcpyAsync(p->h_prev, nrpf::ctl_prev(S), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (*p->h_prev == 0) break;
       }
     } else {
-      int rc = ensure_loop_graph<T>(p);
+      cudaGraphExec_t exec = nullptr;
+      int rc = ensure_loop_graph<T>(p, S, &exec);
       if (rc) return rc;
-      CK(cudaGraphLaunch(p->loop_exec, st));
+      CK(cudaGraphLaunch(exec, st));
     }
   }
   // the last convergence test (iteration ctl->it; nothing is active after an
@@ -457,6 +466,96 @@ int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, doub
   return check_launch();
 }
 
+int pf_solve_batch_host(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
+                        double* v_out, int32_t* iters, uint8_t* status, int chunk, void* stream) {
+  if (!p || p->host_only || B < 0 || maxit < 0 || chunk < 0 || !std::isfinite(tol) || tol < 0)
+    return NRPF_ERR_ARG;
+  if (B == 0) return NRPF_OK;
+  if (!sbus || !v0 || !v_out || !iters || !status) return NRPF_ERR_ARG;
+  if (chunk == 0 || chunk > B) chunk = B;
+  const int n = p->hp.n;
+  int rc = ensure_capacity(p, chunk);
+  if (rc) return rc;
+  // staging slot layout: sbus, v0, v_out [chunk, n] complex; iters [chunk]; status [chunk]
+  const size_t cplx = (size_t)n * 16;
+  auto slot_bytes = [&](int c) { return (size_t)c * (3 * cplx + 4 + 1) + 256; };
+  if (chunk > p->stage_cap) {
+    CK(cudaDeviceSynchronize());
+    for (int i = 0; i < 2; ++i) {
+      if (p->stage_mem[i]) cudaFree(p->stage_mem[i]);
+      p->stage_mem[i] = nullptr;
+    }
+    p->stage_cap = 0;
+    p->slot_used[0] = p->slot_used[1] = false;
+    for (int i = 0; i < 2; ++i) CK(cudaMalloc(&p->stage_mem[i], slot_bytes(chunk)));
+    p->stage_cap = chunk;
+  }
+  if (!p->in_stream) {
+    CK(cudaStreamCreateWithFlags(&p->in_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&p->out_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CK(cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&p->ev_done[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&p->ev_out[i], cudaEventDisableTiming));
+    }
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaStream_t is = p->in_stream, os = p->out_stream;
+  const size_t cap = (size_t)p->stage_cap;
+  struct Slot {
+    double *s, *v0, *v;
+    int32_t* it;
+    uint8_t* st;
+  } slot[2];
+  for (int i = 0; i < 2; ++i) {
+    char* base = reinterpret_cast<char*>(p->stage_mem[i]);
+    slot[i] = {reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + cap * cplx),
+               reinterpret_cast<double*>(base + 2 * cap * cplx), reinterpret_cast<int32_t*>(base + 3 * cap * cplx),
+               reinterpret_cast<uint8_t*>(base + 3 * cap * cplx + cap * 4)};
+  }
+  const int nch = (B + chunk - 1) / chunk;
+  auto first = [&](int c) { return (size_t)c * chunk; };
+  auto count = [&](int c) { return (int)std::min<size_t>(chunk, B - first(c)); };
+  // chunk c's inputs into staging slot i (copy-in stream), once the chunk
+  // that used the slot before has been copied out
+  auto copy_in = [&](int c, int i) -> cudaError_t {
+    const Slot& d = slot[i];
+    cudaError_t e = cudaSuccess;
+    if (p->slot_used[i]) e = cudaStreamWaitEvent(is, p->ev_out[i], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d.s, sbus + first(c) * 2 * n, count(c) * cplx, cudaMemcpyHostToDevice, is);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d.v0, v0 + first(c) * 2 * n, count(c) * cplx, cudaMemcpyHostToDevice, is);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_in[i], is);
+    return e;
+  };
+  int i = p->slot_next;
+  CK(copy_in(0, i));
+  for (int c = 0; c < nch; ++c) {
+    if (c + 1 < nch) CK(copy_in(c + 1, i ^ 1));
+    CK(cudaStreamWaitEvent(st, p->ev_in[i], 0));
+    const Slot& d = slot[i];
+    if (p->lu_precision == NRPF_LU_FP32)
+      rc = enqueue_solve<float>(p, count(c), d.s, d.v0, tol, maxit, d.v, d.it, d.st, st);
+    else
+      rc = enqueue_solve<double>(p, count(c), d.s, d.v0, tol, maxit, d.v, d.it, d.st, st);
+    if (rc) return rc;
+    CK(cudaEventRecord(p->ev_done[i], st));
+    CK(cudaStreamWaitEvent(os, p->ev_done[i], 0));
+    CK(cudaMemcpyAsync(v_out + first(c) * 2 * n, d.v, count(c) * cplx, cudaMemcpyDeviceToHost, os));
+    CK(cudaMemcpyAsync(iters + first(c), d.it, count(c) * 4, cudaMemcpyDeviceToHost, os));
+    CK(cudaMemcpyAsync(status + first(c), d.st, count(c), cudaMemcpyDeviceToHost, os));
+    CK(cudaEventRecord(p->ev_out[i], os));
+    p->slot_used[i] = true;
+    i ^= 1;
+  }
+  p->slot_next = i;
+  // later work on the caller's stream follows the last copy out (the copy-out
+  // stream is in order, so this covers every chunk)
+  CK(cudaStreamWaitEvent(st, p->ev_out[i ^ 1], 0));
+  return check_launch();
+}
+
 int pf_stage_mismatch(pf_plan* p, int B, const double* sbus, const double* v, double* F, double* norm,
                       void* stream) {
   if (!p || p->host_only || B < 0) return NRPF_ERR_ARG;
@@ -560,6 +659,14 @@ void pf_plan_destroy(pf_plan* p) {
   cudaDeviceSynchronize();
   free_ws(p);
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+  for (int i = 0; i < 2; ++i) {
+    if (p->stage_mem[i]) cudaFree(p->stage_mem[i]);
+    if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+    if (p->ev_done[i]) cudaEventDestroy(p->ev_done[i]);
+    if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
+  }
+  if (p->in_stream) cudaStreamDestroy(p->in_stream);
+  if (p->out_stream) cudaStreamDestroy(p->out_stream);
   if (p->h_prev) cudaFreeHost(p->h_prev);
   for (void* a : p->plan_allocs) cudaFree(a);
   if (p->d_pattern_map) cudaFree(p->d_pattern_map);

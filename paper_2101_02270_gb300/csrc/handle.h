@@ -2,6 +2,7 @@
 // translation units that implement entry points).
 #pragma once
 #include <cstdint>
+#include <map>
 #include <vector>
 
 #include "../../include/nrpf.h"
@@ -25,9 +26,23 @@ struct pf_plan {
   // Newton loop as a graph: one iteration captured as the body of a WHILE
   // node whose condition the iteration's last kernel sets (built per
   // workspace; launches of one body by kernel class, for the counters)
-  cudaGraph_t loop_graph = nullptr;
-  cudaGraphExec_t loop_exec = nullptr;
+  struct LoopGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::map<int, LoopGraph> loops;  // by the solve's padded batch (grids cover it)
   cudaStream_t capture_stream = nullptr;
   int64_t body_launches[nrpf::K_NCLASS] = {};
   int32_t* h_prev = nullptr;  // pinned: ctl->prev read back by profiled solves
+  // host-resident batches: two device staging slots of stage_cap instances,
+  // a copy stream and the events that order copies and solves
+  int stage_cap = 0;
+  void* stage_mem[2] = {nullptr, nullptr};
+  cudaStream_t in_stream = nullptr;   // copies host -> device
+  cudaStream_t out_stream = nullptr;  // copies device -> host
+  cudaEvent_t ev_in[2] = {nullptr, nullptr};     // slot's inputs copied in
+  cudaEvent_t ev_done[2] = {nullptr, nullptr};   // slot's chunk solved
+  cudaEvent_t ev_out[2] = {nullptr, nullptr};    // slot's results copied out
+  int slot_next = 0;                            // staging slot of the next chunk
+  bool slot_used[2] = {false, false};           // slot holds a chunk whose copy-out was enqueued
 };

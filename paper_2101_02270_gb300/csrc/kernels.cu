@@ -505,7 +505,7 @@ __global__ void k_dense_panel(DevPlan P, DevState S, int k, int cend, const int3
 // (the 8x8 FP32 tile is latency-bound when registers limit residency)
 template <typename T, int TS>
 struct UpdOcc {
-  static constexpr int value = (sizeof(T) == 4 && TS == 8) ? 3 : 6;
+  static constexpr int value = (sizeof(T) == 4 && TS == 8) ? 2 : 6;
 };
 
 // The updated region is the trailing block [r0, ld) x [r0, ld) without its

@@ -24,6 +24,14 @@ def _dptr(t: torch.Tensor) -> C.c_void_p:
     return C.c_void_p(t.data_ptr())
 
 
+def _hptr(t: torch.Tensor) -> C.c_void_p:
+    if t.device.type != "cpu":
+        raise ValueError("expected a host tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
 def _stream() -> C.c_void_p:
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -111,6 +119,29 @@ class Plan:
             v, iters, status = out
         check(lib.pf_solve_batch(self._h, B, _dptr(sbus), _dptr(v0), float(tol), int(maxit), _dptr(v),
                                  _dptr(iters), _dptr(status), _stream()), "pf_solve_batch")
+        return v, iters, status
+
+    def solve_host(self, sbus: torch.Tensor, v0: torch.Tensor, tol: float = 1e-8, maxit: int = 10,
+                   out=None, chunk: int = 0):
+        """Newton-Raphson for a batch in host memory (complex128 [B, n] CPU
+        tensors, page-locked for overlapped copies): the batch is solved in
+        chunks whose copies overlap the neighbouring chunks' solves
+        (pf_solve_batch_host).  Ordered on the current stream; synchronise it
+        before reading the outputs.  Returns host (v, iters, status)."""
+        B = sbus.shape[0]
+        for t in (sbus, v0):
+            if t.device.type != "cpu" or t.dtype != torch.complex128 or t.shape != (B, self.n) \
+                    or not t.is_contiguous():
+                raise ValueError(f"expected contiguous complex128 [{B}, {self.n}] host tensors")
+        if out is None:
+            pin = sbus.is_pinned()
+            v = torch.empty((B, self.n), dtype=torch.complex128, pin_memory=pin)
+            iters = torch.empty(B, dtype=torch.int32, pin_memory=pin)
+            status = torch.empty(B, dtype=torch.uint8, pin_memory=pin)
+        else:
+            v, iters, status = out
+        check(lib.pf_solve_batch_host(self._h, B, _hptr(sbus), _hptr(v0), float(tol), int(maxit), _hptr(v),
+                                      _hptr(iters), _hptr(status), int(chunk), _stream()), "pf_solve_batch_host")
         return v, iters, status
 
     def stage_mismatch(self, sbus, v):

@@ -284,3 +284,40 @@ def test_loop_graph_matches_host_loops(lu, maxit):
         bodies = maxit
     assert counts["check"][0] == bodies + 1  # plus the final test after the loop
     assert counts["update"][0] == bodies
+
+
+@pytest.mark.parametrize("lu,B,chunk", [("fp64", 100, 32), ("fp32", 100, 0), ("fp64", 64, 64), ("fp64", 45, 200)])
+def test_host_batch_chunks_match_device_solve(lu, B, chunk):
+    """pf_solve_batch_host (chunks copied in and out around the solves,
+    ragged last chunk) gives exactly the device-resident solve's results."""
+    g, S, V0 = case("mesh30_b64", batch=B)
+    with _plan(g, lu_precision=lu) as p:
+        v, it, st = p.solve(_dev(S), _dev(V0), TOL, 10)
+        Sh = torch.from_numpy(np.ascontiguousarray(S)).pin_memory()
+        Vh = torch.from_numpy(np.ascontiguousarray(V0)).pin_memory()
+        vh, ith, sth = p.solve_host(Sh, Vh, TOL, 10, chunk=chunk)
+        torch.cuda.current_stream().synchronize()
+        # pageable host memory works too
+        vp, itp, stp = p.solve_host(torch.from_numpy(np.ascontiguousarray(S)),
+                                    torch.from_numpy(np.ascontiguousarray(V0)), TOL, 10, chunk=chunk)
+        torch.cuda.current_stream().synchronize()
+    for a, b, c in ((v, vh, vp), (it, ith, itp), (st, sth, stp)):
+        assert torch.equal(a.cpu(), b) and torch.equal(a.cpu(), c)
+
+
+def test_host_batch_back_to_back_calls():
+    """Consecutive host-batch calls without a synchronisation in between (the
+    second call's copy-in overlaps the first call's solve) each return the
+    device solve of their own inputs."""
+    g, S1, V0 = case("mesh30_b64", batch=64)
+    S2 = S1 * 0.9
+    with _plan(g) as p:
+        ref = [p.solve(_dev(S), _dev(V0), TOL, 10) for S in (S1, S2, S1)]
+        ref = [tuple(t.cpu() for t in r) for r in ref]
+        hs = [torch.from_numpy(np.ascontiguousarray(S)).pin_memory() for S in (S1, S2, S1)]
+        hv = torch.from_numpy(np.ascontiguousarray(V0)).pin_memory()
+        outs = [p.solve_host(h, hv, TOL, 10) for h in hs]
+        torch.cuda.current_stream().synchronize()
+    for r, o in zip(ref, outs):
+        for a, b in zip(r, o):
+            assert torch.equal(a, b)
