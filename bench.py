@@ -57,7 +57,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="mesh2000_b10k",
-                    choices=list(gridgen.CONFIGS) + ["feeders256x100", "warmstart2000"])
+                    choices=list(gridgen.CONFIGS) + ["feeders256x100", "warmstart2000", "n1_2000"])
     ap.add_argument("--train-samples", type=int, default=200000)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=0, help="override the batch size (0 = the workload's)")
@@ -124,25 +124,52 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_sample(g, S, V0, seconds, cores):
+def _oracle_cases(task):
+    """Oracle Newton solves of instances with their own branch sets (one
+    process of the per-instance-admittance sample)."""
+    from oracle import nrpf
+    n, f, t, r, x, b, bus_type, ins, S, V0 = task
+    st = []
+    for keep, s, v0 in zip(ins, S, V0):
+        Y = nrpf.make_ybus(n, f[keep], t[keep], r[keep], x[keep], b[keep])
+        st.append(nrpf.newton(Y, s, v0, bus_type, TOL, MAXIT)[2])
+    return st
+
+
+def oracle_sample(g, S, V0, seconds, cores, ins=None):
     """Time the CPU oracle on a bounded sample of the workload: a first
     calibration run sizes the sample to about `seconds` of work on `cores`
-    processes."""
+    processes.  ins [B, nbr] (optional): per-instance branch sets, each
+    instance then gets its own admittance matrix."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     from oracle import nrpf
-    Y = nrpf.make_ybus(g.n, g.f, g.t, g.r, g.x, g.b)
+    B = S.shape[0]
+    if ins is None:
+        Y = nrpf.make_ybus(g.n, g.f, g.t, g.r, g.x, g.b)
+        run = lambda k, w: nrpf.newton_batch(Y, S[:k], V0[:k], g.bus_type, TOL, MAXIT, workers=w)[2]
+    else:
+        import multiprocessing as mp
+
+        def run(k, w):
+            if w <= 1 or k < 2:
+                return np.array(_oracle_cases((g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, ins[:k], S[:k], V0[:k])))
+            parts = np.array_split(np.arange(k), min(w, k))
+            tasks = [(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, ins[p], S[p], V0[p]) for p in parts]
+            with mp.get_context("spawn").Pool(len(tasks)) as pool:
+                return np.concatenate([np.array(o) for o in pool.map(_oracle_cases, tasks)])
     t0 = time.perf_counter()
-    nrpf.newton_batch(Y, S[:1], V0[:1], g.bus_type, TOL, MAXIT)
+    run(1, 1)
     t1 = max(time.perf_counter() - t0, 1e-4)
-    size = int(max(cores, min(S.shape[0], seconds * cores / t1)))
-    size = min(size, S.shape[0])
+    size = int(max(cores, min(B, seconds * cores / t1)))
+    size = min(size, B)
     t0 = time.perf_counter()
-    _, it, st = nrpf.newton_batch(Y, S[:size], V0[:size], g.bus_type, TOL, MAXIT, workers=cores)
+    st = run(size, cores)
     dt = time.perf_counter() - t0
     conv = int(np.sum(st == 0))
+    what = "instances (own admittance matrix each)" if ins is not None else "scenarios"
     return {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {size} of {S.shape[0]} scenarios, scipy SuperLU per Newton step, "
+            "sample": f"first {size} of {B} {what}, scipy SuperLU per Newton step, "
                       f"{cores} spawn processes, {dt:.1f} s"}
 
 
@@ -159,6 +186,11 @@ def run_reference(args):
         # a sample mixing feeders: every 16th feeder, its scenarios
         cases = [(fs[i], scen[i].sbus(fs[i]), scen[i].v0_flat(fs[i])) for i in range(0, len(fs), 16)]
         batch = sum(sc.batch for sc in scen)
+    elif name == "n1_2000":
+        g = gridgen.make_grid("mesh2000_b10k")
+        _, _, ins, S = gridgen.n1_batch(g)
+        cases = [(g, S, np.broadcast_to(g.v_set.astype(np.complex128), S.shape).copy(), ins)]
+        batch = int(S.shape[0])
     else:
         gname = "mesh2000_b10k" if name == "warmstart2000" else name
         g = gridgen.make_grid(gname)
@@ -170,8 +202,8 @@ def run_reference(args):
 
     def one(seconds):
         vals, last = [], None
-        for g, S, V0 in cases:
-            last = oracle_sample(g, S, V0, seconds / len(cases), cores)
+        for case in cases:
+            last = oracle_sample(*case[:3], seconds / len(cases), cores, *case[3:])
             vals.append(last["value"])
         return statistics.mean(vals), last
 
@@ -551,9 +583,16 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     name = args.config
-    g = gridgen.make_grid(name)
-    sc = rank_scenarios(name, g, rank, batch=args.batch or None)
-    S_np, V0_np = sc.sbus(g), sc.v0_flat(g)
+    n1 = name == "n1_2000"  # static N-1: every connected single outage x load levels
+    g = gridgen.make_grid("mesh2000_b10k" if n1 else name)
+    ins = None
+    if n1:
+        # rank r scales the load levels by (1 + 0.01 r) (weak scaling)
+        _, _, ins, S_np = gridgen.n1_batch(g, levels=tuple(l * (1 + 0.01 * rank) for l in gridgen.N1_LEVELS))
+        V0_np = np.broadcast_to(g.v_set.astype(np.complex128), S_np.shape).copy()
+    else:
+        sc = rank_scenarios(name, g, rank, batch=args.batch or None)
+        S_np, V0_np = sc.sbus(g), sc.v0_flat(g)
     B = S_np.shape[0]
     S = torch.from_numpy(S_np).to(dev)
     V0 = torch.from_numpy(V0_np).to(dev)
@@ -561,6 +600,8 @@ def run_ours(args):
     plan = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision=args.lu,
                                  dense_frac=args.dense_frac, panel=args.panel, max_batch=B)
     plan_ms = 1e3 * (time.perf_counter() - t0)
+    Y_np = plan.ybus_values(ins) if n1 else None
+    Yd = torch.from_numpy(Y_np).to(dev) if n1 else None
     info = plan.info
     fp64_peak, fp32_peak = pf._lib.fma_peak(C.c_void_p(torch.cuda.current_stream().cuda_stream))
     out = (torch.empty((B, g.n), dtype=torch.complex128, device=dev),
@@ -568,6 +609,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
+        if n1:
+            return plan.solve_y(Yd, S, V0, TOL, args.maxit, out=out)
         return plan.solve(S, V0, TOL, args.maxit, out=out)
 
     for _ in range(max(args.warmup, 0)):
@@ -616,16 +659,32 @@ def run_ours(args):
     V_h = torch.empty((B, g.n), dtype=torch.complex128).pin_memory()
     it_h = torch.empty(B, dtype=torch.int32).pin_memory()
     st_h = torch.empty(B, dtype=torch.uint8).pin_memory()
-    plan.solve_host(S_h, V0_h, TOL, args.maxit, out=(V_h, it_h, st_h), chunk=args.chunk)  # staging warm-up
+    if n1:
+        # per-instance admittances travel too: copies in, solve, copies out
+        Y_h = torch.from_numpy(Y_np).pin_memory()
+        Sd, Vd, Ydd = torch.empty_like(S), torch.empty_like(V0), torch.empty_like(Yd)
+
+        def e2e_step():
+            Ydd.copy_(Y_h, non_blocking=True)
+            Sd.copy_(S_h, non_blocking=True)
+            Vd.copy_(V0_h, non_blocking=True)
+            v, it, st = plan.solve_y(Ydd, Sd, Vd, TOL, args.maxit, out=out)
+            V_h.copy_(v, non_blocking=True)
+            it_h.copy_(it, non_blocking=True)
+            st_h.copy_(st, non_blocking=True)
+    else:
+        def e2e_step():
+            plan.solve_host(S_h, V0_h, TOL, args.maxit, out=(V_h, it_h, st_h), chunk=args.chunk)
+    e2e_step()  # staging warm-up
     barrier()
     e0.record(stream)
     for _ in range(args.steps):
-        plan.solve_host(S_h, V0_h, TOL, args.maxit, out=(V_h, it_h, st_h), chunk=args.chunk)
+        e2e_step()
     e1.record(stream)
     barrier()
     ms_e2e, conv_e2e = combine_ranks(e0.elapsed_time(e1), int(np.sum(st_h.numpy() == 0)), dev)
     e2e_value = conv_e2e * args.steps / (ms_e2e / 1e3)
-    h2d = 2 * B * g.n * 16
+    h2d = 2 * B * g.n * 16 + (Y_np.nbytes if n1 else 0)
     d2h = B * g.n * 16 + B * 4 + B
 
     # ---- roofline of the dominant kernel (dense trailing update) ----
@@ -690,11 +749,17 @@ def run_ours(args):
         "kernel_ms": {k: round(v[2], 3) for k, v in prof.items() if v[1] > 0},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "api": "pf_solve_batch_host (page-locked host buffers, copies overlapped with chunk solves)"},
+                "api": ("pf_solve_batch_y after page-locked host copies of the admittances and injections" if n1
+                        else "pf_solve_batch_host (page-locked host buffers, copies overlapped across calls)")},
         "gpu_launches": launches,
     }
+    if n1:
+        line["config"].update({"contingencies": int(B // len(gridgen.N1_LEVELS)),
+                               "load_levels": list(gridgen.N1_LEVELS),
+                               "case": "every single-branch outage that keeps the grid connected, per-instance "
+                                       "admittances on the base pattern, one injection profile per load level"})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1)
+        line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1, ins)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -15,4 +15,8 @@ from .grids import (  # noqa: F401
     make_feeders,
     config_grid,
     config_scenarios,
+    bridges,
+    n1_contingencies,
+    n1_batch,
+    N1_LEVELS,
 )

@@ -193,3 +193,73 @@ def feeder_scenarios(feeders: list[Grid], per_feeder: int | None = None, seed: i
     per = c["per_feeder"] if per_feeder is None else per_feeder
     rng = np.random.default_rng(seed)
     return [Scenarios(rng.uniform(*c["scen"], size=(per, g.n)), g.load_scale) for g in feeders]
+
+
+# Static N-1 contingency batches: one instance per (branch outage, load level).
+# Only outages that keep the grid connected are listed (a bridge outage would
+# island buses).  The outaged branch keeps its place in the admittance
+# pattern with zero admittance; every instance has the base injections times
+# its load level (one injection profile per level, no per-bus draws).
+N1_LEVELS = (0.8, 0.9, 1.0, 1.1, 1.2)
+
+
+def bridges(n: int, f: np.ndarray, t: np.ndarray) -> np.ndarray:
+    """Boolean [nbr]: branch e is a bridge (its removal disconnects the graph).
+    Parallel branches are never bridges.  Iterative DFS with low-link values
+    (Tarjan), skipping only the branch used to enter a bus."""
+    nbr = len(f)
+    adj = [[] for _ in range(n)]
+    for e in range(nbr):
+        adj[int(f[e])].append((int(t[e]), e))
+        adj[int(t[e])].append((int(f[e]), e))
+    disc = [-1] * n
+    low = [0] * n
+    out = np.zeros(nbr, dtype=bool)
+    timer = 0
+    for root in range(n):
+        if disc[root] >= 0:
+            continue
+        disc[root] = low[root] = timer
+        timer += 1
+        stack = [(root, -1, 0)]  # (bus, entering branch, next adjacency index)
+        while stack:
+            u, pe, i = stack[-1]
+            if i < len(adj[u]):
+                stack[-1] = (u, pe, i + 1)
+                w, e = adj[u][i]
+                if e == pe:
+                    continue
+                if disc[w] < 0:
+                    disc[w] = low[w] = timer
+                    timer += 1
+                    stack.append((w, e, 0))
+                else:
+                    low[u] = min(low[u], disc[w])
+            else:
+                stack.pop()
+                if stack:
+                    p = stack[-1][0]
+                    low[p] = min(low[p], low[u])
+                    if low[u] > disc[p]:
+                        out[pe] = True
+    return out
+
+
+def n1_contingencies(g: Grid) -> np.ndarray:
+    """Indices of the branches whose single outage keeps the grid connected."""
+    return np.flatnonzero(~bridges(g.n, g.f, g.t)).astype(np.int32)
+
+
+def n1_batch(g: Grid, levels=N1_LEVELS):
+    """(outage [B] branch index, level [B] load factor, in_service [B, nbr]
+    bool, sbus [B, n] complex) for every connected single outage at every
+    load level, level-major."""
+    out = n1_contingencies(g)
+    lv = np.asarray(levels, dtype=np.float64)
+    outage = np.tile(out, len(lv))
+    level = np.repeat(lv, len(out))
+    ins = np.ones((len(outage), g.n_branch), dtype=bool)
+    ins[np.arange(len(outage)), outage] = False
+    base = g.p_gen - g.p_load - 1j * g.q_load
+    sbus = (g.load_scale * level)[:, None] * base[None, :]
+    return outage, level, ins, sbus

@@ -146,6 +146,33 @@ int pf_plan_get_pattern(const pf_plan* p, int32_t* pos_of_unknown, int64_t* colp
 int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
                    double* v_out, int32_t* iters, uint8_t* status, void* stream);
 
+/* Per-instance admittance values on the plan's pattern: many Ybus that share
+ * one sparsity pattern, e.g. static N-1 contingency analysis, where each
+ * instance removes a branch (the paper's profile variant with one Ybus per
+ * case and a shared pattern, Sec. 3.2).  The pattern is the plan's (an
+ * outaged branch keeps its entries, with zero admittance).
+ * device in : ybus [B, nnz] complex values in the plan's CRS order (nnz =
+ *             rowptr[n] of pf_plan_create), sbus / v0 [B, n] complex.
+ * device out: as pf_solve_batch.
+ * The values are copied into a workspace array interleaved by instance
+ * (allocated on first use, grown with the batch capacity).
+ * Errors: as pf_solve_batch. */
+int pf_solve_batch_y(pf_plan* p, int B, const double* ybus, const double* sbus, const double* v0, double tol,
+                     int maxit, double* v_out, int32_t* iters, uint8_t* status, void* stream);
+
+/* Host helper for pf_solve_batch_y: Ybus values of B branch-status cases on a
+ * given pattern (MATPOWER pi model as pf_ybus_from_branches; branches out of
+ * service contribute nothing).
+ * host in : n buses, nbr branches f/t/r/x/b [nbr]; in_service [B, nbr]
+ *           (nonzero = in service; NULL = all in service); rowptr [n+1],
+ *           colidx [nnz] with sorted columns per row.
+ * host out: y [B, nnz] complex (re, im interleaved).
+ * Errors: NRPF_ERR_ARG (bad sizes or indices, zero series impedance),
+ * NRPF_ERR_PATTERN (a branch entry missing from the pattern). */
+int pf_ybus_values(int n, int nbr, const int32_t* f, const int32_t* t, const double* r, const double* x,
+                   const double* b, int B, const uint8_t* in_service, const int32_t* rowptr,
+                   const int32_t* colidx, double* y);
+
 /* pf_solve_batch for a batch held in host memory (the paper's stream study,
  * Sec. 3.2 / Sec. 5: copies overlapped with computation).  The batch is cut
  * into chunks of `chunk` instances (0 = the whole batch).  Each chunk goes

@@ -46,7 +46,7 @@ class pf_profile(C.Structure):
 
 
 EXPORTS = ["pf_options_default", "pf_ybus_from_branches", "pf_plan_create", "pf_plan_get_info",
-           "pf_plan_get_pattern", "pf_solve_batch", "pf_solve_batch_host", "pf_stage_mismatch", "pf_stage_factor",
+           "pf_plan_get_pattern", "pf_solve_batch", "pf_solve_batch_host", "pf_solve_batch_y", "pf_ybus_values", "pf_stage_mismatch", "pf_stage_factor",
            "pf_stage_linear_solve", "pf_profile_start", "pf_profile_read", "pf_kernel_class_name",
            "pf_fma_peak", "pf_stage_mismatch_noalloc", "pf_multi_create", "pf_multi_solve",
            "pf_multi_set_config", "pf_multi_get_config", "pf_multi_autotune", "pf_multi_destroy",
@@ -70,6 +70,8 @@ def _load():
     lib.pf_plan_get_pattern.argtypes = [P, P, P, P, C.POINTER(I64)]
     lib.pf_solve_batch.argtypes = [P, I, P, P, D, I, P, P, P, P]
     lib.pf_solve_batch_host.argtypes = [P, I, P, P, D, I, P, P, P, I, P]
+    lib.pf_solve_batch_y.argtypes = [P, I, P, P, P, D, I, P, P, P, P]
+    lib.pf_ybus_values.argtypes = [I, I, P, P, P, P, P, I, P, P, P, P]
     lib.pf_stage_mismatch.argtypes = [P, I, P, P, P, P, P]
     lib.pf_stage_factor.argtypes = [P, I, P, I, P, P]
     lib.pf_stage_linear_solve.argtypes = [P, I, P, P, P, P]
@@ -139,6 +141,27 @@ def ybus_from_branches(n, f, t, r, x, b):
                                     C.byref(nnz)), "pf_ybus_from_branches")
     k = nnz.value
     return rowptr, colidx[:k].copy(), yre[:k].copy(), yim[:k].copy()
+
+
+def ybus_values(n, f, t, r, x, b, rowptr, colidx, in_service=None):
+    """Ybus values [B, nnz] complex128 of B branch-status cases on a given CRS
+    pattern (in_service [B, nbr] bool; None = one case, all in service),
+    computed by the library on the host."""
+    f = np.ascontiguousarray(f, np.int32)
+    t = np.ascontiguousarray(t, np.int32)
+    r = np.ascontiguousarray(r, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    rowptr = np.ascontiguousarray(rowptr, np.int32)
+    colidx = np.ascontiguousarray(colidx, np.int32)
+    nbr = f.shape[0]
+    ins = None if in_service is None else np.ascontiguousarray(in_service, np.uint8).reshape(-1, nbr)
+    B = 1 if ins is None else ins.shape[0]
+    y = np.zeros((B, int(rowptr[n])), np.complex128)
+    check(lib.pf_ybus_values(n, nbr, _np_ptr(f), _np_ptr(t), _np_ptr(r), _np_ptr(x), _np_ptr(b), B,
+                             None if ins is None else _np_ptr(ins), _np_ptr(rowptr), _np_ptr(colidx),
+                             _np_ptr(y)), "pf_ybus_values")
+    return y
 
 
 def fma_peak(stream=None):

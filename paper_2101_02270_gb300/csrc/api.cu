@@ -68,6 +68,9 @@ void destroy_loop_graphs(pf_plan* p) {
 void free_ws(pf_plan* p) {
   fold_graph_launches(p);
   destroy_loop_graphs(p);
+  if (p->yv_mem) cudaFree(p->yv_mem);
+  p->yv_mem = nullptr;
+  p->yv_cap = 0;
   for (void* a : p->ws_allocs) cudaFree(a);
   p->ws_allocs.clear();
   p->capacity = 0;
@@ -147,7 +150,8 @@ void enqueue_body(pf_plan* p, const DevState& S, cudaStream_t st, nrpf::Recorder
 // (or at maxit).
 template <typename T>
 int ensure_loop_graph(pf_plan* p, const DevState& S, cudaGraphExec_t* out) {
-  auto it = p->loops.find(S.Bp);
+  const int key = 2 * S.Bp + (S.yv ? 1 : 0);
+  auto it = p->loops.find(key);
   if (it != p->loops.end()) {
     *out = it->second.exec;
     return NRPF_OK;
@@ -182,21 +186,42 @@ int ensure_loop_graph(pf_plan* p, const DevState& S, cudaGraphExec_t* out) {
   if (e != cudaSuccess) return fail(e);
   cudaGraphExec_t exec = nullptr;
   if ((e = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess) return fail(e);
-  p->loops[S.Bp] = pf_plan::LoopGraph{g, exec};
+  p->loops[key] = pf_plan::LoopGraph{g, exec};
   for (int c = 0; c < nrpf::K_NCLASS; ++c) p->body_launches[c] = count.launches[c];
   *out = exec;
   return NRPF_OK;
 }
 
+// workspace array of per-instance Ybus values for the current capacity
+int ensure_yv(pf_plan* p) {
+  if (p->yv_mem && p->yv_cap >= p->capacity) return NRPF_OK;
+  if (p->yv_mem) {
+    CK(cudaDeviceSynchronize());
+    cudaFree(p->yv_mem);
+    p->yv_mem = nullptr;
+    p->yv_cap = 0;
+  }
+  CK(cudaMalloc(&p->yv_mem, std::max<size_t>((size_t)p->capacity * p->dp.nnzY * 16, 256)));
+  p->yv_cap = p->capacity;
+  return NRPF_OK;
+}
+
+// ybus: per-instance [B, nnzY] complex device values, or null for the plan's
 template <typename T>
-int enqueue_solve(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
-                  double* v_out, int32_t* iters, uint8_t* status, cudaStream_t st) {
+int enqueue_solve(pf_plan* p, int B, const double* ybus, const double* sbus, const double* v0, double tol,
+                  int maxit, double* v_out, int32_t* iters, uint8_t* status, cudaStream_t st) {
   const DevPlan& P = p->dp;
   // grids cover this batch's tiles only (tiles are contiguous per array, so
   // the first Bp of the workspace's capacity serve)
   DevState S = p->st;
   S.Bp = (B + kTile - 1) / kTile * kTile;
   nrpf::Recorder* rec = &p->rec;
+  if (ybus) {
+    int rc = ensure_yv(p);
+    if (rc) return rc;
+    S.yv = reinterpret_cast<const double2*>(p->yv_mem);
+    nrpf::launch_load_y(P, S, B, ybus, st, rec);
+  }
   nrpf::launch_load(P, S, B, sbus, v0, st, rec);
   nrpf::launch_ctl_init(S, maxit, tol, st, rec);
   if (P.m > 0 && maxit > 0) {
@@ -459,11 +484,75 @@ int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, doub
   if (rc) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (p->lu_precision == NRPF_LU_FP32)
-    rc = enqueue_solve<float>(p, B, sbus, v0, tol, maxit, v_out, iters, status, st);
+    rc = enqueue_solve<float>(p, B, nullptr, sbus, v0, tol, maxit, v_out, iters, status, st);
   else
-    rc = enqueue_solve<double>(p, B, sbus, v0, tol, maxit, v_out, iters, status, st);
+    rc = enqueue_solve<double>(p, B, nullptr, sbus, v0, tol, maxit, v_out, iters, status, st);
   if (rc) return rc;
   return check_launch();
+}
+
+int pf_solve_batch_y(pf_plan* p, int B, const double* ybus, const double* sbus, const double* v0, double tol,
+                     int maxit, double* v_out, int32_t* iters, uint8_t* status, void* stream) {
+  if (!p || p->host_only || B < 0 || maxit < 0 || !std::isfinite(tol) || tol < 0) return NRPF_ERR_ARG;
+  if (B == 0) return NRPF_OK;
+  if (!ybus || !sbus || !v0 || !v_out || !iters || !status) return NRPF_ERR_ARG;
+  int rc = ensure_capacity(p, B);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (p->lu_precision == NRPF_LU_FP32)
+    rc = enqueue_solve<float>(p, B, ybus, sbus, v0, tol, maxit, v_out, iters, status, st);
+  else
+    rc = enqueue_solve<double>(p, B, ybus, sbus, v0, tol, maxit, v_out, iters, status, st);
+  if (rc) return rc;
+  return check_launch();
+}
+
+int pf_ybus_values(int n, int nbr, const int32_t* f, const int32_t* t, const double* r, const double* x,
+                   const double* b, int B, const uint8_t* in_service, const int32_t* rowptr,
+                   const int32_t* colidx, double* y) {
+  if (n <= 0 || nbr < 0 || B < 0 || !rowptr || !y) return NRPF_ERR_ARG;
+  if (nbr > 0 && (!f || !t || !r || !x || !b)) return NRPF_ERR_ARG;
+  const int64_t nnz = rowptr[n];
+  if (rowptr[0] != 0 || nnz < 0 || (nnz > 0 && !colidx)) return NRPF_ERR_ARG;
+  // pattern position of (i, k): binary search in row i's sorted columns
+  auto find = [&](int i, int k) -> int64_t {
+    const int32_t* lo = colidx + rowptr[i];
+    const int32_t* hi = colidx + rowptr[i + 1];
+    const int32_t* q = std::lower_bound(lo, hi, k);
+    return (q != hi && *q == k) ? (int64_t)(q - colidx) : -1;
+  };
+  struct Stamp {
+    int64_t ff, tt, ft, tf;
+    double gs, bs, bh;
+  };
+  std::vector<Stamp> st(nbr);
+  for (int e = 0; e < nbr; ++e) {
+    const int a = f[e], c = t[e];
+    if (a < 0 || a >= n || c < 0 || c >= n) return NRPF_ERR_ARG;
+    const double den = r[e] * r[e] + x[e] * x[e];
+    if (!(den > 0.0) || !std::isfinite(den) || !std::isfinite(b[e])) return NRPF_ERR_ARG;
+    Stamp s{find(a, a), find(c, c), find(a, c), find(c, a), r[e] / den, -x[e] / den, 0.5 * b[e]};
+    if (s.ff < 0 || s.tt < 0 || s.ft < 0 || s.tf < 0) return NRPF_ERR_PATTERN;
+    st[e] = s;
+  }
+  for (int k = 0; k < B; ++k) {
+    double* yk = y + (size_t)k * nnz * 2;
+    std::fill(yk, yk + nnz * 2, 0.0);
+    const uint8_t* ins = in_service ? in_service + (size_t)k * nbr : nullptr;
+    for (int e = 0; e < nbr; ++e) {
+      if (ins && !ins[e]) continue;
+      const Stamp& s = st[e];
+      yk[2 * s.ff] += s.gs;
+      yk[2 * s.ff + 1] += s.bs + s.bh;
+      yk[2 * s.tt] += s.gs;
+      yk[2 * s.tt + 1] += s.bs + s.bh;
+      yk[2 * s.ft] -= s.gs;
+      yk[2 * s.ft + 1] -= s.bs;
+      yk[2 * s.tf] -= s.gs;
+      yk[2 * s.tf + 1] -= s.bs;
+    }
+  }
+  return NRPF_OK;
 }
 
 int pf_solve_batch_host(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
@@ -536,9 +625,9 @@ int pf_solve_batch_host(pf_plan* p, int B, const double* sbus, const double* v0,
     CK(cudaStreamWaitEvent(st, p->ev_in[i], 0));
     const Slot& d = slot[i];
     if (p->lu_precision == NRPF_LU_FP32)
-      rc = enqueue_solve<float>(p, count(c), d.s, d.v0, tol, maxit, d.v, d.it, d.st, st);
+      rc = enqueue_solve<float>(p, count(c), nullptr, d.s, d.v0, tol, maxit, d.v, d.it, d.st, st);
     else
-      rc = enqueue_solve<double>(p, count(c), d.s, d.v0, tol, maxit, d.v, d.it, d.st, st);
+      rc = enqueue_solve<double>(p, count(c), nullptr, d.s, d.v0, tol, maxit, d.v, d.it, d.st, st);
     if (rc) return rc;
     CK(cudaEventRecord(p->ev_done[i], st));
     CK(cudaStreamWaitEvent(os, p->ev_done[i], 0));
@@ -659,6 +748,7 @@ void pf_plan_destroy(pf_plan* p) {
   cudaDeviceSynchronize();
   free_ws(p);
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+  if (p->yv_mem) cudaFree(p->yv_mem);
   for (int i = 0; i < 2; ++i) {
     if (p->stage_mem[i]) cudaFree(p->stage_mem[i]);
     if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);

@@ -84,6 +84,7 @@ struct DevState {
   int32_t* active;  // [Bp]
   int32_t* bad;     // [Bp] non-finite step detected
   SolveCtl* ctl;  // Newton loop control (one per workspace)
+  const double2* yv;  // [nnzY] per-instance Ybus values (re, im), or null: the plan's shared values
 };
 
 }  // namespace nrpf

@@ -30,7 +30,7 @@ struct pf_plan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
   };
-  std::map<int, LoopGraph> loops;  // by the solve's padded batch (grids cover it)
+  std::map<int, LoopGraph> loops;  // by 2 x padded batch + per-instance Ybus flag
   cudaStream_t capture_stream = nullptr;
   int64_t body_launches[nrpf::K_NCLASS] = {};
   int32_t* h_prev = nullptr;  // pinned: ctl->prev read back by profiled solves
@@ -43,6 +43,8 @@ struct pf_plan {
   cudaEvent_t ev_in[2] = {nullptr, nullptr};     // slot's inputs copied in
   cudaEvent_t ev_done[2] = {nullptr, nullptr};   // slot's chunk solved
   cudaEvent_t ev_out[2] = {nullptr, nullptr};    // slot's results copied out
+  void* yv_mem = nullptr;  // per-instance Ybus values, capacity x nnzY complex
+  int yv_cap = 0;
   int slot_next = 0;                            // staging slot of the next chunk
   bool slot_used[2] = {false, false};           // slot holds a chunk whose copy-out was enqueued
 };

@@ -151,6 +151,19 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
   const double* __restrict__ ve = S.ve + (size_t)tile * P.n * kTile;
   const double* __restrict__ vf = S.vf + (size_t)tile * P.n * kTile;
   const double* __restrict__ vinv = S.vinv + (size_t)tile * P.n * kTile;
+  // per-instance admittances (interleaved like every per-instance array) or
+  // the plan's shared ones; the choice is uniform over the launch
+  const double2* __restrict__ Yv = S.yv ? S.yv + (size_t)tile * P.nnzY * kTile + lane : nullptr;
+  auto yval = [&](int d, double& G, double& Bv) {
+    if (Yv) {
+      const double2 y = Yv[(size_t)d * kTile];
+      G = y.x;
+      Bv = y.y;
+    } else {
+      G = P.yre[d];
+      Bv = P.yim[d];
+    }
+  };
   double nrm = 0.0;
   const int ibeg = (blockIdx.x * kMWarps + warp) * kBusPerWarp;
   for (int ii = 0; ii < kBusPerWarp; ++ii) {
@@ -163,7 +176,8 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
     const int d0 = P.rowptr[i], d1 = P.rowptr[i + 1];
     for (int d = d0; d < d1; ++d) {
       const int k = P.colidx[d];
-      const double G = P.yre[d], Bv = P.yim[d];
+      double G, Bv;
+      yval(d, G, Bv);
       const double ek = ve[k * kTile + lane], fk = vf[k * kTile + lane];
       const double yr = G * ek - Bv * fk;
       const double yi = G * fk + Bv * ek;
@@ -199,7 +213,8 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
     if (jac) {
       const int dd = P.ydiag[i];
       const int4 jm = reinterpret_cast<const int4*>(P.jmap)[dd];
-      const double G = P.yre[dd], Bv = P.yim[dd];
+      double G, Bv;
+      yval(dd, G, Bv);
       const double vm2 = ei * ei + fi * fi;
       const double ivm = vinv[o];
       const double vm = vm2 * ivm;
@@ -217,6 +232,22 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
     double r = red[0][lane];
     for (int w = 1; w < kMWarps; ++w) r = fmax(r, red[w][lane]);
     atomicMax(&S.norm[tile * kTile + lane], (unsigned long long)__double_as_longlong(r));
+  }
+}
+
+// Per-instance Ybus values: user [B, nnzY] complex -> interleaved tiles,
+// through a 32-entry x 32-instance tile in shared memory (block (32, 8)).
+__global__ void k_load_y(int nnzY, int B, const double2* __restrict__ y, double2* __restrict__ yv) {
+  __shared__ double2 t[32][33];
+  const int d0 = blockIdx.x * 32, tile = blockIdx.y;
+  for (int r = threadIdx.y; r < 32; r += 8) {  // r = instance within the tile
+    const int b = tile * kTile + r, d = d0 + threadIdx.x;
+    t[r][threadIdx.x] = (b < B && d < nnzY) ? y[(size_t)b * nnzY + d] : make_double2(0.0, 0.0);
+  }
+  __syncthreads();
+  for (int c = threadIdx.y; c < 32; c += 8) {  // c = entry within the block
+    const int d = d0 + c;
+    if (d < nnzY) yv[((size_t)tile * nnzY + d) * kTile + threadIdx.x] = t[threadIdx.x][c];
   }
 }
 
@@ -866,6 +897,13 @@ void launch_mismatch(const DevPlan& P, const DevState& S, int jac, const int32_t
                      Recorder* rec) {
   dim3 g((P.n + kMWarps * kBusPerWarp - 1) / (kMWarps * kBusPerWarp), S.Bp / kTile);
   NRPF_LAUNCH(rec, K_MISMATCH, st, k_mismatch_jac<T><<<g, dim3(32, kMWarps), 0, st>>>(P, S, jac, gate));
+}
+
+void launch_load_y(const DevPlan& P, const DevState& S, int B, const double* y, cudaStream_t st, Recorder* rec) {
+  dim3 g((P.nnzY + 31) / 32, S.Bp / kTile);
+  NRPF_LAUNCH(rec, K_LOAD, st,
+              k_load_y<<<g, dim3(32, 8), 0, st>>>(P.nnzY, B, reinterpret_cast<const double2*>(y),
+                                                  const_cast<double2*>(S.yv)));
 }
 
 void launch_ctl_init(const DevState& S, int maxit, double tol, cudaStream_t st, Recorder* rec) {

@@ -27,6 +27,10 @@ inline const int32_t* ctl_cur(const DevState& S) {
   return reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(S.ctl) + offsetof(SolveCtl, cur));
 }
 
+// Per-instance Ybus values [B, nnzY] complex into S.yv (interleaved).
+void launch_load_y(const DevPlan& P, const DevState& S, int B, const double* y, cudaStream_t st,
+                   Recorder* rec = nullptr);
+
 // Reset the loop control (prev = 1, cur = 0, it = 0) with the tolerance and
 // iteration limit of this solve.
 void launch_ctl_init(const DevState& S, int maxit, double tol, cudaStream_t st, Recorder* rec = nullptr);

@@ -65,7 +65,16 @@ class Plan:
     @classmethod
     def from_branches(cls, n, f, t, r, x, b, bus_type, **kw):
         rowptr, colidx, yre, yim = _lib.ybus_from_branches(n, f, t, r, x, b)
-        return cls(n, rowptr, colidx, yre, yim, bus_type, **kw)
+        plan = cls(n, rowptr, colidx, yre, yim, bus_type, **kw)
+        plan._branches = (f, t, r, x, b)
+        return plan
+
+    def ybus_values(self, in_service=None) -> np.ndarray:
+        """Ybus values [B, nnz] complex128 on this plan's pattern for B
+        branch-status cases (in_service [B, nbr] bool); the plan must come
+        from from_branches."""
+        f, t, r, x, b = self._branches
+        return _lib.ybus_values(self.n, f, t, r, x, b, self._rowptr, self._colidx, in_service)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -119,6 +128,28 @@ class Plan:
             v, iters, status = out
         check(lib.pf_solve_batch(self._h, B, _dptr(sbus), _dptr(v0), float(tol), int(maxit), _dptr(v),
                                  _dptr(iters), _dptr(status), _stream()), "pf_solve_batch")
+        return v, iters, status
+
+    def solve_y(self, ybus: torch.Tensor, sbus: torch.Tensor, v0: torch.Tensor, tol: float = 1e-8,
+                maxit: int = 10, out=None):
+        """Newton-Raphson with per-instance admittances on this plan's pattern
+        (pf_solve_batch_y): ybus complex128 [B, nnz] on the GPU in the
+        pattern's CRS order, sbus / v0 complex128 [B, n] on the GPU."""
+        B = sbus.shape[0]
+        self._check_bn(sbus, B)
+        self._check_bn(v0, B)
+        nnz = int(self._rowptr[self.n])
+        if ybus.dtype != torch.complex128 or ybus.shape != (B, nnz):
+            raise ValueError(f"expected complex128 [{B}, {nnz}], got {ybus.dtype} {tuple(ybus.shape)}")
+        dev = sbus.device
+        if out is None:
+            v = torch.empty((B, self.n), dtype=torch.complex128, device=dev)
+            iters = torch.empty(B, dtype=torch.int32, device=dev)
+            status = torch.empty(B, dtype=torch.uint8, device=dev)
+        else:
+            v, iters, status = out
+        check(lib.pf_solve_batch_y(self._h, B, _dptr(ybus), _dptr(sbus), _dptr(v0), float(tol), int(maxit),
+                                   _dptr(v), _dptr(iters), _dptr(status), _stream()), "pf_solve_batch_y")
         return v, iters, status
 
     def solve_host(self, sbus: torch.Tensor, v0: torch.Tensor, tol: float = 1e-8, maxit: int = 10,
