@@ -251,8 +251,8 @@ def combine_ranks(ms, converged, device):
 # GPU arm
 # ---------------------------------------------------------------------------
 # ncu DRAM bytes over algorithmic bytes of the depth-64 FP32 trailing update
-# (373.2 MB of 419.4 MB, profiles/dense_update_fp32_mesh2000.md).
-DENSE_UPDATE_FP32_DRAM_PER_ALG = 373.2 / 419.4
+# (371.7 MB of 419.4 MB, profiles/dense_update_fp32_mesh2000.md).
+DENSE_UPDATE_FP32_DRAM_PER_ALG = 371.7 / 419.4
 
 KERNEL_TIMING = ("CUDA events around every dense_update launch on its stream, during a second pass of the "
                  "K timed steps")
