@@ -173,6 +173,39 @@ int pf_ybus_values(int n, int nbr, const int32_t* f, const int32_t* t, const dou
                    const double* b, int B, const uint8_t* in_service, const int32_t* rowptr,
                    const int32_t* colidx, double* y);
 
+/* Second chance for failed instances (Sec. 3.2: cases whose refactorisation
+ * without pivoting breaks down are solved again with a pivoting
+ * factorisation).  Newton-Raphson on the host cores with a left-looking
+ * sparse LU that picks each pivot row among the rows not yet pivoted
+ * (threshold 0.1 towards the diagonal) in the plan's column order; same
+ * tolerance, iteration and status conventions as pf_solve_batch.
+ *
+ * pf_solve_pivoting_host: host in sbus / v0 [B, n] complex; host out v_out
+ * [B, n], iters [B], status [B].  Works on host-only plans.  Synchronous.
+ *
+ * pf_retry_failed: after a pf_solve_batch on `stream` (device arrays of that
+ * call), synchronises the stream, re-solves from v0 every instance whose
+ * status is NRPF_FAILED and writes its v_out / iters / status back to the
+ * device; *n_retried (may be NULL) receives the count.  Synchronous.
+ * Errors: NRPF_ERR_ARG, NRPF_ERR_CUDA. */
+int pf_solve_pivoting_host(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
+                           double* v_out, int32_t* iters, uint8_t* status);
+int pf_retry_failed(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
+                    double* v_out, int32_t* iters, uint8_t* status, int* n_retried, void* stream);
+
+/* Branch power flows of solved batches (post-processing after convergence,
+ * Sec. 3.2): the complex power entering each branch at its from end (sf) and
+ * at its to end (st), pi model as pf_ybus_from_branches; sf + st is the
+ * branch's loss.
+ * device in : f, t [nbr] bus indices, r, x, b [nbr] branch data;
+ *             in_service [B, nbr] (nonzero = in service; NULL = all; a branch
+ *             out of service carries zero flow); v [B, n] complex voltages.
+ * device out: sf, st [B, nbr] complex.
+ * Asynchronous on `stream`.  Errors: NRPF_ERR_ARG, NRPF_ERR_CUDA. */
+int pf_branch_flows(int n, int nbr, const int32_t* f, const int32_t* t, const double* r, const double* x,
+                    const double* b, int B, const uint8_t* in_service, const double* v, double* sf, double* st,
+                    void* stream);
+
 /* pf_solve_batch for a batch held in host memory (the paper's stream study,
  * Sec. 3.2 / Sec. 5: copies overlapped with computation).  The batch is cut
  * into chunks of `chunk` instances (0 = the whole batch).  Each chunk goes

@@ -70,6 +70,29 @@ def make_ybus(n, f, t, r, x, b):
     return Y
 
 
+def branch_flows(f, t, r, x, b, V):
+    """Complex power entering each branch at its two ends (the post-processing
+    after convergence that the paper's second-chance step precedes, Sec. 3.2).
+
+    pi model: series admittance ys = 1/(r + jx), half of the line charging b at
+    each end.  The current leaving bus f into the branch is
+    I_f = ys (V_f - V_t) + j b/2 V_f, and symmetrically I_t at bus t; the power
+    entering the branch there is S_f = V_f conj(I_f), S_t = V_t conj(I_t).
+    Written branch by branch.  Returns (Sf, St) complex128 [nbr].
+    """
+    nbr = len(f)
+    Sf = np.zeros(nbr, np.complex128)
+    St = np.zeros(nbr, np.complex128)
+    for e in range(nbr):
+        vf, vt = V[int(f[e])], V[int(t[e])]
+        ys = 1.0 / complex(r[e], x[e])
+        i_f = ys * (vf - vt) + 0.5j * b[e] * vf
+        i_t = ys * (vt - vf) + 0.5j * b[e] * vt
+        Sf[e] = vf * np.conj(i_f)
+        St[e] = vt * np.conj(i_t)
+    return Sf, St
+
+
 def bus_sets(bus_type):
     """Index sets (ascending): slack, PV, PQ and PV+PQ (the angle unknowns)."""
     bt = np.asarray(bus_type)

@@ -130,6 +130,61 @@ class Plan:
                                  _dptr(iters), _dptr(status), _stream()), "pf_solve_batch")
         return v, iters, status
 
+    def solve_pivoting_host(self, sbus: np.ndarray, v0: np.ndarray, tol: float = 1e-8, maxit: int = 10):
+        """Newton-Raphson on the host cores with a pivoting sparse LU
+        (pf_solve_pivoting_host): numpy complex128 [B, n] in, numpy
+        (v, iters, status) out.  Works on host-only plans."""
+        S = np.ascontiguousarray(sbus, np.complex128)
+        V0 = np.ascontiguousarray(v0, np.complex128)
+        B = S.shape[0]
+        if S.shape != (B, self.n) or V0.shape != (B, self.n):
+            raise ValueError(f"expected complex128 [{B}, {self.n}]")
+        v = np.empty_like(S)
+        it = np.empty(B, np.int32)
+        st = np.empty(B, np.uint8)
+        check(lib.pf_solve_pivoting_host(self._h, B, _lib._np_ptr(S), _lib._np_ptr(V0), float(tol), int(maxit),
+                                         _lib._np_ptr(v), _lib._np_ptr(it), _lib._np_ptr(st)), "pf_solve_pivoting_host")
+        return v, it, st
+
+    def retry_failed(self, sbus: torch.Tensor, v0: torch.Tensor, out, tol: float = 1e-8, maxit: int = 10) -> int:
+        """Second chance (pf_retry_failed): re-solve with the pivoting host
+        solver every instance of a finished solve (device arrays sbus, v0 and
+        out = (v, iters, status)) whose status is 2; returns how many."""
+        B = sbus.shape[0]
+        self._check_bn(sbus, B)
+        self._check_bn(v0, B)
+        v, iters, status = out
+        n = C.c_int(0)
+        check(lib.pf_retry_failed(self._h, B, _dptr(sbus), _dptr(v0), float(tol), int(maxit), _dptr(v),
+                                  _dptr(iters), _dptr(status), C.byref(n), _stream()), "pf_retry_failed")
+        return n.value
+
+    def branch_flows(self, v: torch.Tensor, in_service: torch.Tensor = None):
+        """Power entering every branch at its from and to ends (pf_branch_flows)
+        for solved voltages v complex128 [B, n] on the GPU; in_service [B, nbr]
+        bool/uint8 on the GPU or None.  The plan must come from from_branches.
+        Returns (sf, st) complex128 [B, nbr]."""
+        B = v.shape[0]
+        self._check_bn(v, B)
+        if getattr(self, "_dev_branches", None) is None or self._dev_branches[0].device != v.device:
+            f, t, r, x, b = self._branches
+            self._dev_branches = tuple(torch.from_numpy(np.ascontiguousarray(a, dt)).to(v.device)
+                                       for a, dt in ((f, np.int32), (t, np.int32), (r, np.float64),
+                                                     (x, np.float64), (b, np.float64)))
+        f, t, r, x, b = self._dev_branches
+        nbr = f.shape[0]
+        ins = None
+        if in_service is not None:
+            if in_service.shape != (B, nbr):
+                raise ValueError(f"in_service must be [{B}, {nbr}]")
+            ins = in_service.to(torch.uint8).contiguous()
+        sf = torch.empty((B, nbr), dtype=torch.complex128, device=v.device)
+        st = torch.empty((B, nbr), dtype=torch.complex128, device=v.device)
+        check(lib.pf_branch_flows(self.n, nbr, _dptr(f), _dptr(t), _dptr(r), _dptr(x), _dptr(b), B,
+                                  None if ins is None else _dptr(ins), _dptr(v), _dptr(sf), _dptr(st), _stream()),
+              "pf_branch_flows")
+        return sf, st
+
     def solve_y(self, ybus: torch.Tensor, sbus: torch.Tensor, v0: torch.Tensor, tol: float = 1e-8,
                 maxit: int = 10, out=None):
         """Newton-Raphson with per-instance admittances on this plan's pattern

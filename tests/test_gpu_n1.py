@@ -88,3 +88,29 @@ def test_n1_mesh2000_full_batch_sampled():
     rng = np.random.default_rng(0)
     idx = [0, len(outage) - 1] + list(rng.choice(len(outage), 6, replace=False))
     _check(g, ins, S, V0, Vg, itg, stg, idx)
+
+
+def test_branch_flows_against_oracle():
+    """Branch flows of solved N-1 cases: every end against the oracle's
+    branch-by-branch formula at the GPU's voltages (outaged branches carry
+    nothing), and the flows at each bus add up to its specified injection."""
+    g = gridgen.make_grid("mesh30_b64")
+    outage, level, ins, S = gridgen.n1_batch(g)
+    V0 = np.broadcast_to(g.v_set.astype(np.complex128), S.shape).copy()
+    with _plan(g) as p:
+        Y = p.ybus_values(ins)
+        v, it, st = p.solve_y(_dev(Y), _dev(S), _dev(V0), TOL, 10)
+        sf, stt = p.branch_flows(v, torch.from_numpy(ins).cuda())
+        Vg, sf, stt = v.cpu().numpy(), sf.cpu().numpy(), stt.cpu().numpy()
+        assert np.all(st.cpu().numpy() == 0)
+    _, pv, pq, _ = nrpf.bus_sets(g.bus_type)
+    for k in range(0, len(outage), 7):
+        keep = ins[k]
+        Sfo, Sto = nrpf.branch_flows(g.f[keep], g.t[keep], g.r[keep], g.x[keep], g.b[keep], Vg[k])
+        assert np.max(np.abs(sf[k][keep] - Sfo)) < 1e-12 and np.max(np.abs(stt[k][keep] - Sto)) < 1e-12
+        assert np.all(sf[k][~keep] == 0) and np.all(stt[k][~keep] == 0)
+        acc = np.zeros(g.n, complex)
+        np.add.at(acc, g.f, sf[k])
+        np.add.at(acc, g.t, stt[k])
+        assert np.max(np.abs(acc[pq] - S[k][pq])) < 1e-8
+        assert np.max(np.abs(acc.real[pv] - S[k].real[pv])) < 1e-8

@@ -321,3 +321,33 @@ def test_tolerance_threshold_is_strict():
         assert (it, st) == (k + 1, nrpf.STATUS_CONVERGED)
         _, it, st = nrpf.newton(Y, S[0], V0[0], g.bus_type, tol=h[k] / 1.5)
         assert (it, st) == (k + 1, nrpf.STATUS_CONVERGED)
+
+
+def test_branch_flows_sum_to_nodal_injections():
+    """Kirchhoff: at every bus the powers entering its branch ends add up to
+    the nodal injection V conj(Y V) of the independently assembled Ybus, at any
+    V (no bus shunts in these grids)."""
+    g, Y, S, V0 = _mesh30()
+    rng = np.random.default_rng(8)
+    V = (1 + 0.05 * rng.standard_normal(g.n)) * np.exp(0.1j * rng.standard_normal(g.n))
+    Sf, St = nrpf.branch_flows(g.f, g.t, g.r, g.x, g.b, V)
+    acc = np.zeros(g.n, complex)
+    np.add.at(acc, g.f, Sf)
+    np.add.at(acc, g.t, St)
+    assert np.max(np.abs(acc - nrpf.power_injection(Y, V))) < 1e-12
+
+
+def test_branch_flows_closed_form_losses():
+    """S_f + S_t = conj(ys) |V_f - V_t|^2 - j b/2 (|V_f|^2 + |V_t|^2) per
+    branch, and a lossless open-ended line (V_t = V_f) carries only its
+    charging."""
+    g, Y, S, V0 = _mesh30()
+    rng = np.random.default_rng(9)
+    V = (1 + 0.05 * rng.standard_normal(g.n)) * np.exp(0.1j * rng.standard_normal(g.n))
+    Sf, St = nrpf.branch_flows(g.f, g.t, g.r, g.x, g.b, V)
+    ys = 1.0 / (g.r + 1j * g.x)
+    vf, vt = V[g.f], V[g.t]
+    want = np.conj(ys) * np.abs(vf - vt) ** 2 - 0.5j * g.b * (np.abs(vf) ** 2 + np.abs(vt) ** 2)
+    assert np.max(np.abs(Sf + St - want)) < 1e-12
+    Sf1, St1 = nrpf.branch_flows([0], [1], [0.02], [0.1], [0.04], np.array([1.02 + 0.0j, 1.02 + 0.0j]))
+    assert abs(Sf1[0] - (-0.02j * 1.02 ** 2)) < 1e-15 and abs(St1[0] - Sf1[0]) < 1e-15
