@@ -458,13 +458,41 @@ def run_warmstart(args):
     clocks.start()
     time.sleep(0.3)
     ms_flat64, (vf, itf, stf) = timed(lambda: plan64.solve(Sh, Vh, TOL, MAXIT))
+    plan64.profile_start([])
     ms_warm64, (vw, itw, stw, fb) = timed(lambda: ws64.solve(Sh, Vh, TOL, MAXIT))
+    prof = plan64.profile_read()
+    # library launches of the timed warm solves: the plan's (solves, including
+    # any flat-start fallback) plus the network's per guess: features, v0 and,
+    # per chunk of bmax instances, input scaling + three GEMMs + output scaling
+    # (the counters also saw the warm-up calls: scale to the timed ones)
+    calls = max(args.warmup, 1) + args.steps
+    per_call = sum(v[0] for v in prof.values()) / calls + 2 + 5 * -(-S_np.shape[0] // net.bmax)
+    launches = int(round(per_call * args.steps))
     ms_flat32, (vf32, itf32, stf32) = timed(lambda: plan32.solve(Sh, Vh, TOL, 20))
     ms_warm32, (vw32, itw32, stw32, fb32) = timed(lambda: ws32.solve(Sh, Vh, TOL, 20))
     clk = clocks.stop()
     B = S_np.shape[0]
     conv = int((stw == 0).sum().item())
     value = conv / (ms_warm64 / 1e3)
+    # end to end: page-locked host scenarios in, warm-started solve, results out
+    S_pin = torch.from_numpy(S_np).pin_memory()
+    V_pin = torch.from_numpy(V0_np).pin_memory()
+    Sd, Vd = torch.empty_like(Sh), torch.empty_like(Vh)
+    v_pin = torch.empty((B, g.n), dtype=torch.complex128).pin_memory()
+    it_pin = torch.empty(B, dtype=torch.int32).pin_memory()
+    st_pin = torch.empty(B, dtype=torch.uint8).pin_memory()
+
+    def e2e():
+        Sd.copy_(S_pin, non_blocking=True)
+        Vd.copy_(V_pin, non_blocking=True)
+        v, it, st, _ = ws64.solve(Sd, Vd, TOL, MAXIT)
+        v_pin.copy_(v, non_blocking=True)
+        it_pin.copy_(it, non_blocking=True)
+        st_pin.copy_(st, non_blocking=True)
+        return None
+
+    ms_e2e, _ = timed(e2e)
+    e2e_value = int((st_pin == 0).sum()) / (ms_e2e / 1e3)
     dv = float((vw - vf).abs().max().item())
     # oracle check of a sample of warm-started results
     from oracle import nrpf
@@ -489,7 +517,9 @@ def run_warmstart(args):
                         "iters_mean": float(itf32.float().mean())},
         "max_dv_warm_vs_flat": dv, "max_dv_warm_vs_oracle_sample": d_or,
         "training": {"generate_s": round(gen_s, 2), "train_s": round(train_s, 2), "final_loss": final_loss},
-        "clocks": clk, "gpu_launches": None,
+        "clocks": clk, "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * S_pin.nbytes),
+                "d2h_bytes_per_step": int(v_pin.nbytes + it_pin.nbytes + st_pin.nbytes)},
     }
     print(json.dumps(line), flush=True)
 
