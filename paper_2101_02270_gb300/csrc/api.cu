@@ -415,9 +415,19 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
       (rc = upload(p, h.bw_ptr, &d.bw_ptr)) || (rc = upload(p, h.bw_pos, &d.bw_pos)) ||
       (rc = upload(p, h.bw_col, &d.bw_col)) || (rc = upload(p, h.unk_pos, &d.unk_pos)) ||
       (rc = upload(p, h.lu_lvl_ptr, &d.lu_lvl_ptr)) || (rc = upload(p, h.fw_lvl_ptr, &d.fw_lvl_ptr)) ||
-      (rc = upload(p, h.bw_lvl_ptr, &d.bw_lvl_ptr))) {
+      (rc = upload(p, h.bw_lvl_ptr, &d.bw_lvl_ptr)) || (rc = upload(p, h.schur_kit, &d.schur_kit)) ||
+      (rc = upload(p, h.schur_ent, &d.schur_ent)) || (rc = upload(p, h.schur_mask, &d.schur_mask))) {
     pf_plan_destroy(p);
     return rc;
+  }
+  {
+    const int32_t* tasks = nullptr;
+    if ((rc = upload(p, h.schur_task, &tasks))) {
+      pf_plan_destroy(p);
+      return rc;
+    }
+    d.schur_task = reinterpret_cast<const int4*>(tasks);
+    d.n_schur = (int)(h.schur_task.size() / 4);
   }
   if (o.max_batch > 0 && (rc = ensure_capacity(p, o.max_batch))) {
     pf_plan_destroy(p);

@@ -382,6 +382,55 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
   }
 }
 
+// Schur complement of the sparse columns into the dense block, after the
+// sparse levels (every U(k, j) is then final).  A warp per (dense column j,
+// chunk of 32 dense rows) and tile: the products L(i, k) U(k, j) of all
+// sparse columns k are summed per row in shared memory (one column of 32
+// rows per lane), then subtracted from A(i, j) once.  Entries of one k-item
+// have distinct rows, so their shared-memory updates are independent.
+constexpr int kSchurWarps = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kSchurWarps) k_schur(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
+  if (gate && *gate == 0) return;
+  __shared__ T acc[kSchurWarps][32][32];
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const int t = blockIdx.x * kSchurWarps + w;
+  const int tile = blockIdx.y;
+  if (t >= P.n_schur) return;
+  if (!tile_active(S, tile, lane)) return;
+  T* __restrict__ LUb = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;
+  const T* __restrict__ LU = LUb + lane;  // sparse positions (< NS): p * 32
+  T(*a)[32] = acc[w];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) a[r][lane] = (T)0;
+  const int4 task = P.schur_task[t];
+  for (int q = task.z; q < task.w; ++q) {
+    const int ukj = P.schur_kit[3 * q], e0 = P.schur_kit[3 * q + 1], e1 = P.schur_kit[3 * q + 2];
+    const T u = LU[(size_t)ukj * kTile];
+    int e = e0;
+    for (; e + 4 <= e1; e += 4) {
+      const int32_t x0 = P.schur_ent[e], x1 = P.schur_ent[e + 1], x2 = P.schur_ent[e + 2], x3 = P.schur_ent[e + 3];
+      const T l0 = LU[(size_t)(x0 >> 5) * kTile], l1 = LU[(size_t)(x1 >> 5) * kTile];
+      const T l2 = LU[(size_t)(x2 >> 5) * kTile], l3 = LU[(size_t)(x3 >> 5) * kTile];
+      a[x0 & 31][lane] += l0 * u;
+      a[x1 & 31][lane] += l1 * u;
+      a[x2 & 31][lane] += l2 * u;
+      a[x3 & 31][lane] += l3 * u;
+    }
+    for (; e < e1; ++e) {
+      const int32_t x = P.schur_ent[e];
+      a[x & 31][lane] += LU[(size_t)(x >> 5) * kTile] * u;
+    }
+  }
+  // A(i, j) -= sum, for the rows that received something
+  const uint32_t mask = P.schur_mask[t];
+  const int64_t col = P.NS + (int64_t)task.x * P.ndp + 32 * task.y;
+#pragma unroll 4
+  for (int r = 0; r < 32; ++r)
+    if (mask >> r & 1u) LUb[lu_off<T>(col + r, P.NS, lane)] -= a[r][lane];
+}
+
 // ---------------------------------------------------------------------------
 // Dense trailing block: right-looking blocked LU without pivoting, panel width
 // kb, on every instance's ndp x ndp column-major block (Sec. 4.3: the serial
@@ -989,6 +1038,9 @@ void launch_factor(const DevPlan& P, const DevState& S, const std::vector<int32_
                 k_lu_sparse_level<T><<<grid2(c1 - c0, kLWarps, tiles), dim3(32, kLWarps), 0, st>>>(P, S, c0, c1,
                                                                                                   gate));
   }
+  if (P.n_schur > 0)
+    NRPF_LAUNCH(rec, K_LU_SPARSE, st,
+                k_schur<T><<<grid2(P.n_schur, kSchurWarps, tiles), dim3(32, kSchurWarps), 0, st>>>(P, S, gate));
   for (int k = 0; k < P.ndp; k += P.kb) {
     if (P.kb == 4) launch_dense_step<T, 4>(P, S, k, P.ndp, P.ndp, gate, st, rec);
     else if (P.kb == 8) launch_dense_step<T, 8>(P, S, k, P.ndp, P.ndp, gate, st, rec);

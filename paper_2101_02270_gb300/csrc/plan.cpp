@@ -200,26 +200,62 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
   P.upd.clear();
   P.dst.clear();
   double fma = 0;
+  for (int k = 0; k < s; ++k)
+    if (!std::is_sorted(Lpat[k].begin(), Lpat[k].end())) { err = "internal: L pattern not sorted"; return NRPF_ERR_PATTERN; }
+  P.schur_task.clear(); P.schur_kit.clear(); P.schur_ent.clear(); P.schur_mask.clear();
   for (int j = 0; j < m; ++j) {
     int lv = 0;
     for (int k : Ustr[j]) {  // k < s, ascending
       lv = std::max(lv, level[k] + 1);
+      // rows of L(:, k) below s go to the level schedule; for a dense column
+      // the rows >= s (ascending, after them) go to the Schur tasks
+      int nsp = (int)Lpat[k].size();
+      if (j >= s) nsp = (int)(std::lower_bound(Lpat[k].begin(), Lpat[k].end(), s) - Lpat[k].begin());
+      fma += (double)Lpat[k].size();
+      if (nsp == 0) continue;
       Upd u;
       u.ukj = (int32_t)P.pos(k, j);
       u.lsrc = P.dp[k] + 1;
-      u.llen = (int32_t)(P.ce[k] - P.dp[k] - 1);
+      u.llen = nsp;
       u.dst_off = (int32_t)P.dst.size();
-      if (P.dst.size() + Lpat[k].size() >= ((size_t)1 << 31)) {
+      if (P.dst.size() + nsp >= ((size_t)1 << 31)) {
         err = "refactor schedule exceeds 2^31 updates (use the AMD ordering)";
         return NRPF_ERR_NOMEM;
       }
-      for (int i : Lpat[k]) {
-        int64_t pp = P.pos(i, j);
+      for (int q = 0; q < nsp; ++q) {
+        int64_t pp = P.pos(Lpat[k][q], j);
         if (pp < 0) { err = "internal: fill pattern not closed"; return NRPF_ERR_PATTERN; }
         P.dst.push_back((int32_t)pp);
       }
-      fma += u.llen;
       P.upd.push_back(u);
+    }
+    if (j >= s && P.nd > 0) {
+      const int nch = (P.nd + 31) / 32;
+      for (int c = 0; c < nch; ++c) {
+        const int kit0 = (int)P.schur_kit.size() / 3;
+        uint32_t mask = 0;
+        for (int k : Ustr[j]) {
+          const int e0 = (int)P.schur_ent.size();
+          auto it = std::lower_bound(Lpat[k].begin(), Lpat[k].end(), s + 32 * c);
+          for (; it != Lpat[k].end() && *it < s + 32 * c + 32; ++it) {
+            const int64_t lpos = P.dp[k] + 1 + (it - Lpat[k].begin());
+            if (lpos >= ((int64_t)1 << 26)) { err = "LU too large for the Schur task encoding"; return NRPF_ERR_NOMEM; }
+            const int r = *it - s - 32 * c;
+            P.schur_ent.push_back((int32_t)((lpos << 5) | r));
+            mask |= 1u << r;
+          }
+          if ((int)P.schur_ent.size() > e0) {
+            P.schur_kit.push_back((int32_t)P.pos(k, j));
+            P.schur_kit.push_back(e0);
+            P.schur_kit.push_back((int32_t)P.schur_ent.size());
+          }
+        }
+        const int kit1 = (int)P.schur_kit.size() / 3;
+        if (kit1 > kit0) {
+          P.schur_task.insert(P.schur_task.end(), {j - s, c, kit0, kit1});
+          P.schur_mask.push_back(mask);
+        }
+      }
     }
     level[j] = lv;
     P.col_upd_ptr[j + 1] = (int32_t)P.upd.size();

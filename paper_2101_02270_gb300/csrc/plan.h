@@ -45,6 +45,15 @@ struct HostPlan {
   std::vector<int32_t> col_upd_ptr;              // [m+1] into upd
   std::vector<Upd> upd;
   std::vector<int32_t> dst;
+  // ---- Schur complement of the sparse columns into the dense block ----
+  // The updates of a dense column j by sparse columns k keep only their rows
+  // < s in the level schedule (they finish U(k, j)); the rows >= s are applied
+  // afterwards, all dense columns at once, by tasks of (dense column, chunk of
+  // 32 dense rows): schur_task[4t..] = {j - s, chunk, first k-item, end};
+  // k-item q: schur_kit[3q..] = {position of U(k, j), first entry, end};
+  // entry: (position of L(i, k) << 5) | (i - s - 32 chunk).
+  std::vector<int32_t> schur_task, schur_kit, schur_ent;
+  std::vector<uint32_t> schur_mask;  // [tasks] rows of the chunk that receive updates
   // ---- forward / backward substitution schedules (row-oriented) ----
   std::vector<int32_t> fw_lvl_ptr, fw_rows, fw_ptr, fw_pos, fw_col;
   std::vector<int32_t> bw_lvl_ptr, bw_rows, bw_ptr, bw_pos, bw_col;
