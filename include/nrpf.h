@@ -364,7 +364,8 @@ int pf_warmstart_v0(int n, int B, const int32_t* nsidx, const int8_t* bus_type, 
  * Kernel classes (index into the pf_profile arrays): 0 load (input transpose),
  * 1 store, 2 mismatch_jacobian, 3 check, 4 zero_lu, 5 set_ones,
  * 6 lu_sparse_level, 7 dense_diag, 8 dense_panel, 9 dense_update, 10 fwd_level,
- * 11 dense_solve, 12 bwd_level, 13 update, 14 aux. */
+ * 11 dense_solve, 12 bwd_level, 13 update, 14 aux, 15 lu_schur (the sparse
+ * columns' updates of the dense block). */
 #define NRPF_KCLASSES 16
 typedef struct pf_profile {
   int64_t launches[NRPF_KCLASSES];  /* kernels enqueued by pf_solve_batch        */

@@ -415,7 +415,7 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
       (rc = upload(p, h.bw_ptr, &d.bw_ptr)) || (rc = upload(p, h.bw_pos, &d.bw_pos)) ||
       (rc = upload(p, h.bw_col, &d.bw_col)) || (rc = upload(p, h.unk_pos, &d.unk_pos)) ||
       (rc = upload(p, h.lu_lvl_ptr, &d.lu_lvl_ptr)) || (rc = upload(p, h.fw_lvl_ptr, &d.fw_lvl_ptr)) ||
-      (rc = upload(p, h.bw_lvl_ptr, &d.bw_lvl_ptr)) || (rc = upload(p, h.schur_kit, &d.schur_kit)) ||
+      (rc = upload(p, h.bw_lvl_ptr, &d.bw_lvl_ptr)) || (rc = upload(p, h.schur_u, &d.schur_u)) ||
       (rc = upload(p, h.schur_ent, &d.schur_ent)) || (rc = upload(p, h.schur_mask, &d.schur_mask))) {
     pf_plan_destroy(p);
     return rc;
@@ -741,7 +741,7 @@ int pf_profile_read(pf_plan* p, pf_profile* out) {
 const char* pf_kernel_class_name(int c) {
   static const char* names[] = {"load", "store", "mismatch_jacobian", "check", "zero_lu", "set_ones",
                                 "lu_sparse_level", "dense_diag", "dense_panel", "dense_update", "fwd_level",
-                                "dense_solve", "bwd_level", "update", "aux"};
+                                "dense_solve", "bwd_level", "update", "aux", "lu_schur"};
   if (c < 0 || c >= nrpf::K_NCLASS) return "unknown";
   return names[c];
 }

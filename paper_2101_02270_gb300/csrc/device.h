@@ -42,9 +42,9 @@ struct DevPlan {
   const int32_t* dp;           // [m] diagonal position (-1 for dense columns)
   const int64_t* ce;           // [m] segment end
   // Schur complement of the sparse columns into the dense block
-  const int4* schur_task;     // {dense column, 32-row chunk, first k-item, end}
-  const int32_t* schur_kit;   // 3 per k-item: U(k, j) position, first entry, end
-  const int32_t* schur_ent;   // (L position << 5) | row in chunk
+  const int4* schur_task;     // {dense column, 32-row chunk, first entry, end}
+  const int32_t* schur_ent;   // (L(i, k) position << 5) | row in chunk
+  const int32_t* schur_u;     // U(k, j) position of the entry
   const uint32_t* schur_mask; // rows of the chunk that receive updates
   int n_schur;
   // FS/BS

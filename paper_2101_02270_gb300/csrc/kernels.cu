@@ -386,8 +386,9 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
 // sparse levels (every U(k, j) is then final).  A warp per (dense column j,
 // chunk of 32 dense rows) and tile: the products L(i, k) U(k, j) of all
 // sparse columns k are summed per row in shared memory (one column of 32
-// rows per lane), then subtracted from A(i, j) once.  Entries of one k-item
-// have distinct rows, so their shared-memory updates are independent.
+// rows per lane), then subtracted from A(i, j) once.  The warp reads 32
+// entries with one coalesced load and hands them out by shuffles, so the
+// L and U loads of eight entries are in flight together.
 constexpr int kSchurWarps = 4;
 
 template <typename T>
@@ -405,30 +406,53 @@ __global__ void __launch_bounds__(32 * kSchurWarps) k_schur(DevPlan P, DevState 
 #pragma unroll
   for (int r = 0; r < 32; ++r) a[r][lane] = (T)0;
   const int4 task = P.schur_task[t];
-  for (int q = task.z; q < task.w; ++q) {
-    const int ukj = P.schur_kit[3 * q], e0 = P.schur_kit[3 * q + 1], e1 = P.schur_kit[3 * q + 2];
-    const T u = LU[(size_t)ukj * kTile];
-    int e = e0;
-    for (; e + 4 <= e1; e += 4) {
-      const int32_t x0 = P.schur_ent[e], x1 = P.schur_ent[e + 1], x2 = P.schur_ent[e + 2], x3 = P.schur_ent[e + 3];
-      const T l0 = LU[(size_t)(x0 >> 5) * kTile], l1 = LU[(size_t)(x1 >> 5) * kTile];
-      const T l2 = LU[(size_t)(x2 >> 5) * kTile], l3 = LU[(size_t)(x3 >> 5) * kTile];
-      a[x0 & 31][lane] += l0 * u;
-      a[x1 & 31][lane] += l1 * u;
-      a[x2 & 31][lane] += l2 * u;
-      a[x3 & 31][lane] += l3 * u;
-    }
-    for (; e < e1; ++e) {
-      const int32_t x = P.schur_ent[e];
-      a[x & 31][lane] += LU[(size_t)(x >> 5) * kTile] * u;
+  for (int eb = task.z; eb < task.w; eb += 32) {
+    const int cnt = min(32, task.w - eb);
+    const int32_t xl = lane < cnt ? P.schur_ent[eb + lane] : 0;
+    const int32_t ul = lane < cnt ? P.schur_u[eb + lane] : 0;
+    for (int i = 0; i < cnt; i += 8) {
+      T l[8], u[8];
+      int r[8];
+#pragma unroll
+      for (int z = 0; z < 8; ++z) {
+        const int32_t x = __shfl_sync(0xffffffffu, xl, i + z);
+        const int32_t up = __shfl_sync(0xffffffffu, ul, i + z);
+        r[z] = x & 31;
+        const bool ok = i + z < cnt;
+        l[z] = ok ? LU[(size_t)(x >> 5) * kTile] : (T)0;
+        u[z] = ok ? LU[(size_t)up * kTile] : (T)0;
+      }
+      // entries of one task keep their order: sums per row accumulate in
+      // the order of the sparse columns
+#pragma unroll
+      for (int z = 0; z < 8; ++z)
+        if (i + z < cnt) a[r[z]][lane] += l[z] * u[z];
     }
   }
   // A(i, j) -= sum, for the rows that received something
   const uint32_t mask = P.schur_mask[t];
-  const int64_t col = P.NS + (int64_t)task.x * P.ndp + 32 * task.y;
+  if constexpr (DenseGroup<T>::G == 4) {
+    // grouped FP32 block: rows 4g .. 4g+3 of the chunk are one 16-byte word
+    // per lane (rows without updates subtract an exact zero)
+    float4* __restrict__ A4 = reinterpret_cast<float4*>(LUb + (size_t)P.NS * kTile);
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      const int r0 = 32 * task.y + 4 * g;
+      if (!(mask >> (4 * g) & 0xFu) || r0 >= P.ndp) continue;
+      float4* q = A4 + ((size_t)task.x * P.ndp + r0) * 8 + lane;
+      float4 v = *q;
+      v.x -= a[4 * g][lane];
+      v.y -= a[4 * g + 1][lane];
+      v.z -= a[4 * g + 2][lane];
+      v.w -= a[4 * g + 3][lane];
+      *q = v;
+    }
+  } else {
+    const int64_t col = P.NS + (int64_t)task.x * P.ndp + 32 * task.y;
 #pragma unroll 4
-  for (int r = 0; r < 32; ++r)
-    if (mask >> r & 1u) LUb[lu_off<T>(col + r, P.NS, lane)] -= a[r][lane];
+    for (int r = 0; r < 32; ++r)
+      if (mask >> r & 1u) LUb[lu_off<T>(col + r, P.NS, lane)] -= a[r][lane];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1039,7 +1063,7 @@ void launch_factor(const DevPlan& P, const DevState& S, const std::vector<int32_
                                                                                                   gate));
   }
   if (P.n_schur > 0)
-    NRPF_LAUNCH(rec, K_LU_SPARSE, st,
+    NRPF_LAUNCH(rec, K_SCHUR, st,
                 k_schur<T><<<grid2(P.n_schur, kSchurWarps, tiles), dim3(32, kSchurWarps), 0, st>>>(P, S, gate));
   for (int k = 0; k < P.ndp; k += P.kb) {
     if (P.kb == 4) launch_dense_step<T, 4>(P, S, k, P.ndp, P.ndp, gate, st, rec);

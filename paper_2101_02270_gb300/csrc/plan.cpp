@@ -202,7 +202,7 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
   double fma = 0;
   for (int k = 0; k < s; ++k)
     if (!std::is_sorted(Lpat[k].begin(), Lpat[k].end())) { err = "internal: L pattern not sorted"; return NRPF_ERR_PATTERN; }
-  P.schur_task.clear(); P.schur_kit.clear(); P.schur_ent.clear(); P.schur_mask.clear();
+  P.schur_task.clear(); P.schur_ent.clear(); P.schur_u.clear(); P.schur_mask.clear();
   for (int j = 0; j < m; ++j) {
     int lv = 0;
     for (int k : Ustr[j]) {  // k < s, ascending
@@ -232,27 +232,23 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
     if (j >= s && P.nd > 0) {
       const int nch = (P.nd + 31) / 32;
       for (int c = 0; c < nch; ++c) {
-        const int kit0 = (int)P.schur_kit.size() / 3;
+        const int e0 = (int)P.schur_ent.size();
         uint32_t mask = 0;
         for (int k : Ustr[j]) {
-          const int e0 = (int)P.schur_ent.size();
+          const int32_t ukj = (int32_t)P.pos(k, j);
           auto it = std::lower_bound(Lpat[k].begin(), Lpat[k].end(), s + 32 * c);
           for (; it != Lpat[k].end() && *it < s + 32 * c + 32; ++it) {
             const int64_t lpos = P.dp[k] + 1 + (it - Lpat[k].begin());
             if (lpos >= ((int64_t)1 << 26)) { err = "LU too large for the Schur task encoding"; return NRPF_ERR_NOMEM; }
             const int r = *it - s - 32 * c;
             P.schur_ent.push_back((int32_t)((lpos << 5) | r));
+            P.schur_u.push_back(ukj);
             mask |= 1u << r;
           }
-          if ((int)P.schur_ent.size() > e0) {
-            P.schur_kit.push_back((int32_t)P.pos(k, j));
-            P.schur_kit.push_back(e0);
-            P.schur_kit.push_back((int32_t)P.schur_ent.size());
-          }
         }
-        const int kit1 = (int)P.schur_kit.size() / 3;
-        if (kit1 > kit0) {
-          P.schur_task.insert(P.schur_task.end(), {j - s, c, kit0, kit1});
+        if ((int)P.schur_ent.size() > e0) {
+          if (P.schur_ent.size() >= ((size_t)1 << 31)) { err = "Schur task list exceeds 2^31 entries"; return NRPF_ERR_NOMEM; }
+          P.schur_task.insert(P.schur_task.end(), {j - s, c, e0, (int32_t)P.schur_ent.size()});
           P.schur_mask.push_back(mask);
         }
       }

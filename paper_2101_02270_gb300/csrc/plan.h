@@ -49,10 +49,10 @@ struct HostPlan {
   // The updates of a dense column j by sparse columns k keep only their rows
   // < s in the level schedule (they finish U(k, j)); the rows >= s are applied
   // afterwards, all dense columns at once, by tasks of (dense column, chunk of
-  // 32 dense rows): schur_task[4t..] = {j - s, chunk, first k-item, end};
-  // k-item q: schur_kit[3q..] = {position of U(k, j), first entry, end};
-  // entry: (position of L(i, k) << 5) | (i - s - 32 chunk).
-  std::vector<int32_t> schur_task, schur_kit, schur_ent;
+  // 32 dense rows): schur_task[4t..] = {j - s, chunk, first entry, end};
+  // entry e: schur_ent[e] = (position of L(i, k) << 5) | (i - s - 32 chunk),
+  // schur_u[e] = position of U(k, j).
+  std::vector<int32_t> schur_task, schur_ent, schur_u;
   std::vector<uint32_t> schur_mask;  // [tasks] rows of the chunk that receive updates
   // ---- forward / backward substitution schedules (row-oriented) ----
   std::vector<int32_t> fw_lvl_ptr, fw_rows, fw_ptr, fw_pos, fw_col;

@@ -12,7 +12,7 @@ namespace nrpf {
 
 enum KClass : int {
   K_LOAD = 0, K_STORE, K_MISMATCH, K_CHECK, K_ZERO, K_ONES, K_LU_SPARSE, K_DENSE_DIAG,
-  K_DENSE_PANEL, K_DENSE_UPDATE, K_FWD, K_DENSE_SOLVE, K_BWD, K_UPDATE, K_AUX, K_NCLASS
+  K_DENSE_PANEL, K_DENSE_UPDATE, K_FWD, K_DENSE_SOLVE, K_BWD, K_UPDATE, K_AUX, K_SCHUR, K_NCLASS
 };
 
 struct Recorder {

@@ -13,7 +13,7 @@ from ._lib import check, lib
 
 _PREC = {"fp64": _lib.LU_FP64, "fp32": _lib.LU_FP32}
 _ORDER = {"amd": _lib.ORDER_AMD, "natural": _lib.ORDER_NATURAL}
-KERNEL_CLASSES = [lib.pf_kernel_class_name(i).decode() for i in range(15)]
+KERNEL_CLASSES = [lib.pf_kernel_class_name(i).decode() for i in range(16)]
 
 
 def _dptr(t: torch.Tensor) -> C.c_void_p:
