@@ -186,13 +186,15 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
       if (jac && k != i) {
         const int4 jm = reinterpret_cast<const int4*>(P.jmap)[d];
         if (jm.x >= 0) {
-          const double Wr = ei * yr + fi * yi;
-          const double Wi = fi * yr - ei * yi;
-          const double ik = vinv[k * kTile + lane];
-          LU[lu_off<T>(jm.x, P.NS, lane)] = (T)Wi;
-          if (jm.y >= 0) LU[lu_off<T>(jm.y, P.NS, lane)] = (T)(Wr * ik);
-          if (jm.z >= 0) LU[lu_off<T>(jm.z, P.NS, lane)] = (T)(-Wr);
-          if (jm.w >= 0) LU[lu_off<T>(jm.w, P.NS, lane)] = (T)(Wi * ik);
+          // off-diagonal Jacobian entries, formed in the LU precision (they
+          // are stored in it; the mismatch above stays FP64)
+          const T Wr = (T)ei * (T)yr + (T)fi * (T)yi;
+          const T Wi = (T)fi * (T)yr - (T)ei * (T)yi;
+          const T ik = (T)vinv[k * kTile + lane];
+          LU[lu_off<T>(jm.x, P.NS, lane)] = Wi;
+          if (jm.y >= 0) LU[lu_off<T>(jm.y, P.NS, lane)] = Wr * ik;
+          if (jm.z >= 0) LU[lu_off<T>(jm.z, P.NS, lane)] = -Wr;
+          if (jm.w >= 0) LU[lu_off<T>(jm.w, P.NS, lane)] = Wi * ik;
         }
       }
     }
