@@ -141,6 +141,14 @@ int pf_plan_get_pattern(const pf_plan* p, int32_t* pos_of_unknown, int64_t* colp
  * stream    : cudaStream_t of the caller (NULL = legacy default stream).
  * Asynchronous: returns after enqueueing.  Grows the workspace (device
  * allocation, synchronous) when B exceeds the plan's capacity.
+ * The Newton loop ends on the device: one iteration is captured once per
+ * padded batch size as the body of a CUDA graph WHILE node, and the
+ * iteration's last kernel clears the condition when no instance is active
+ * (or at maxit).  Inside a caller's stream capture the loop is enqueued as
+ * maxit iterations instead (finished instances skip through their gates);
+ * with per-kernel timing on (pf_profile_start with a nonzero mask) the host
+ * ends the loop after each iteration.  All three give identical results.
+ * Calls on one plan share its workspace: serialise them (one stream).
  * Errors: NRPF_ERR_ARG (B < 0, tol not finite, maxit < 0, null pointers),
  * NRPF_ERR_NOMEM, NRPF_ERR_CUDA.  B == 0 is a no-op. */
 int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,

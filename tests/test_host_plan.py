@@ -158,3 +158,31 @@ def test_ybus_builder_rejects_bad_branches():
         pf.ybus_from_branches(3, [0], [5], [0.1], [0.1], [0.0])  # bus out of range
     with pytest.raises(pf.NrpfError):
         pf.ybus_from_branches(3, [0], [1], [0.0], [0.0], [0.0])  # zero impedance
+
+
+def test_dense_update_accounting_matches_lu_arithmetic():
+    """bench.py's algorithmic flop count of the dense updates: for any panel
+    scheme, updates + panel work = the textbook count of a right-looking LU
+    without pivoting, sum over k of (n-k-1) + (n-k-1)^2 multiply-adds; the
+    two-level schemes do the same multiply-adds as one-level panels of 16."""
+    import importlib.util
+    import pathlib
+    spec = importlib.util.spec_from_file_location("bench", pathlib.Path(__file__).parent.parent / "bench.py")
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    n = 320
+    total = sum((n - k - 1) + (n - k - 1) ** 2 for k in range(n))
+    for kb in (4, 8, 16, 32, 64):
+        upd = bench.dense_update_flop(n, kb) // 2
+        # within-panel work of a one-level panel of width w at column k:
+        # every elimination inside the panel touches the panel's rows below
+        inner = 16 if kb > 16 else kb
+        panel = 0
+        for k in range(0, n, inner):
+            for c in range(inner):
+                r = n - k - c - 1
+                panel += r + r * (inner - c - 1)  # L column scaling + updates inside the panel's columns
+        # the rows of the panel to the right (U12): every column right of the panel
+        u12 = sum((n - k - inner) * sum(range(inner)) for k in range(0, n, inner))
+        assert upd + panel + u12 == total, kb
+    assert bench.dense_update_flop(n, 32) == bench.dense_update_flop(n, 16) == bench.dense_update_flop(n, 64)
