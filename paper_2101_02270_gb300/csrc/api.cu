@@ -135,7 +135,7 @@ void enqueue_body(pf_plan* p, const DevState& S, cudaStream_t st, nrpf::Recorder
   const HostPlan& h = p->hp;
   const int32_t* prev = nrpf::ctl_prev(S);
   const int32_t* cur = nrpf::ctl_cur(S);
-  nrpf::launch_prepare_lu<T>(P, S, prev, st, rec);
+  nrpf::launch_prepare_lu<T>(P, S, prev, st, rec, false);
   nrpf::launch_mismatch<T>(P, S, 1, prev, st, rec);
   nrpf::launch_check(S, st, rec);
   nrpf::launch_factor<T>(P, S, h.lu_lvl_ptr, cur, st, rec);
@@ -416,7 +416,7 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
       (rc = upload(p, h.bw_col, &d.bw_col)) || (rc = upload(p, h.unk_pos, &d.unk_pos)) ||
       (rc = upload(p, h.lu_lvl_ptr, &d.lu_lvl_ptr)) || (rc = upload(p, h.fw_lvl_ptr, &d.fw_lvl_ptr)) ||
       (rc = upload(p, h.bw_lvl_ptr, &d.bw_lvl_ptr)) || (rc = upload(p, h.schur_u, &d.schur_u)) ||
-      (rc = upload(p, h.schur_ent, &d.schur_ent)) || (rc = upload(p, h.schur_mask, &d.schur_mask))) {
+      (rc = upload(p, h.schur_ent, &d.schur_ent)) || (rc = upload(p, h.schur_jmask, &d.schur_jmask))) {
     pf_plan_destroy(p);
     return rc;
   }

@@ -45,7 +45,7 @@ struct DevPlan {
   const int4* schur_task;     // {dense column, 32-row chunk, first entry, end}
   const int32_t* schur_ent;   // (L(i, k) position << 5) | row in chunk
   const int32_t* schur_u;     // U(k, j) position of the entry
-  const uint32_t* schur_mask; // rows of the chunk that receive updates
+  const uint32_t* schur_jmask; // rows of the chunk holding a Jacobian entry
   int n_schur;
   // FS/BS
   const int32_t* fw_rows; const int32_t* fw_ptr; const int32_t* fw_pos; const int32_t* fw_col;

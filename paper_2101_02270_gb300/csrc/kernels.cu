@@ -77,11 +77,14 @@ __global__ void k_load(DevPlan P, DevState S, int B, const double2* __restrict__
     if (i >= P.n) continue;
     double2 s = ss[tx][c], v = sv[tx][c];
     size_t o = sidx(tile, P.n, i, tx);
-    double vm = sqrt(v.x * v.x + v.y * v.y);
+    // a start on the positive real axis (flat start) needs no FP64 sqrt or
+    // atan2: |V| is the real part itself and the angle 0
+    const bool real = v.y == 0.0 && v.x > 0.0;
+    double vm = real ? v.x : sqrt(v.x * v.x + v.y * v.y);
     S.psp[o] = s.x;
     S.qsp[o] = s.y;
     S.vm[o] = vm;
-    S.va[o] = atan2(v.y, v.x);
+    S.va[o] = real ? 0.0 : atan2(v.y, v.x);
     S.ve[o] = v.x;
     S.vf[o] = v.y;
     S.vinv[o] = 1.0 / vm;
@@ -309,11 +312,15 @@ __global__ void k_iter_tail(SolveCtl* c, cudaGraphConditionalHandle cond, int gr
 
 // Zero a buffer (16-byte stores, grid-stride), skipped once no instance is
 // active.
-__global__ void k_zero16(uint4* __restrict__ p, size_t n16, const int32_t* __restrict__ gate) {
+// Zero the first n16 16-byte words of each of `tiles` arrays spaced stride16
+// words apart (the LU arrays of the tiles: whole, or their sparse segments).
+__global__ void k_zero16(uint4* __restrict__ p, size_t n16, size_t stride16, int tiles,
+                         const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;
   const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (size_t)gridDim.x * blockDim.x)
-    p[i] = z;
+  const size_t total = n16 * (size_t)tiles;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    p[(i / n16) * stride16 + i % n16] = z;
 }
 
 // Identity on the padding of the dense block, and zero right-hand side on
@@ -326,10 +333,13 @@ __global__ void k_set_ones(DevPlan P, DevState S, const int32_t* __restrict__ ga
   const int tile = blockIdx.y, lane = threadIdx.x;
   T* LU = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;
   T* X = reinterpret_cast<T*>(S.x) + (size_t)tile * P.mp * kTile;
-  for (int t = threadIdx.y; t < P.n_one; t += blockDim.y) {
-    LU[lu_off<T>(P.one_pos[t], P.NS, lane)] = (T)1;
-    X[(size_t)(P.m + t) * kTile + lane] = (T)0;
+  // padding columns nd .. ndp-1 of the dense block: whole identity columns
+  // (the refactorisation does not zero the dense block)
+  for (int q = threadIdx.y; q < P.n_one * P.ndp; q += blockDim.y) {
+    const int t = q / P.ndp, r = q % P.ndp;
+    LU[lu_off<T>(P.NS + (int64_t)(P.nd + t) * P.ndp + r, P.NS, lane)] = (T)(r == P.nd + t ? 1 : 0);
   }
+  for (int t = threadIdx.y; t < P.n_one; t += blockDim.y) X[(size_t)(P.m + t) * kTile + lane] = (T)0;
 }
 
 // ---------------------------------------------------------------------------
@@ -431,29 +441,35 @@ __global__ void __launch_bounds__(32 * kSchurWarps) k_schur(DevPlan P, DevState 
         if (i + z < cnt) a[r[z]][lane] += l[z] * u[z];
     }
   }
-  // A(i, j) -= sum, for the rows that received something
-  const uint32_t mask = P.schur_mask[t];
+  // every row of the chunk below the padded size: A(i, j) = J(i, j) or 0,
+  // minus the sum (the block is not zeroed before the refactorisation; the
+  // Jacobian fill has written its entries)
+  const uint32_t jm = P.schur_jmask[t];
   if constexpr (DenseGroup<T>::G == 4) {
     // grouped FP32 block: rows 4g .. 4g+3 of the chunk are one 16-byte word
-    // per lane (rows without updates subtract an exact zero)
+    // per lane
     float4* __restrict__ A4 = reinterpret_cast<float4*>(LUb + (size_t)P.NS * kTile);
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
       const int r0 = 32 * task.y + 4 * g;
-      if (!(mask >> (4 * g) & 0xFu) || r0 >= P.ndp) continue;
+      if (r0 >= P.ndp) break;
       float4* q = A4 + ((size_t)task.x * P.ndp + r0) * 8 + lane;
-      float4 v = *q;
-      v.x -= a[4 * g][lane];
-      v.y -= a[4 * g + 1][lane];
-      v.z -= a[4 * g + 2][lane];
-      v.w -= a[4 * g + 3][lane];
+      const uint32_t jb = jm >> (4 * g) & 0xFu;
+      float4 v = jb ? *q : make_float4(0.f, 0.f, 0.f, 0.f);
+      v.x = (jb & 1u) ? v.x - a[4 * g][lane] : -a[4 * g][lane];
+      v.y = (jb & 2u) ? v.y - a[4 * g + 1][lane] : -a[4 * g + 1][lane];
+      v.z = (jb & 4u) ? v.z - a[4 * g + 2][lane] : -a[4 * g + 2][lane];
+      v.w = (jb & 8u) ? v.w - a[4 * g + 3][lane] : -a[4 * g + 3][lane];
       *q = v;
     }
   } else {
     const int64_t col = P.NS + (int64_t)task.x * P.ndp + 32 * task.y;
+    const int nr = min(32, P.ndp - 32 * task.y);
 #pragma unroll 4
-    for (int r = 0; r < 32; ++r)
-      if (mask >> r & 1u) LUb[lu_off<T>(col + r, P.NS, lane)] -= a[r][lane];
+    for (int r = 0; r < nr; ++r) {
+      T* q = LUb + lu_off<T>(col + r, P.NS, lane);
+      *q = (jm >> r & 1u) ? *q - a[r][lane] : -a[r][lane];
+    }
   }
 }
 
@@ -996,12 +1012,17 @@ void launch_iter_tail(const DevState& S, cudaGraphConditionalHandle cond, int gr
 
 template <typename T>
 void launch_prepare_lu(const DevPlan& P, const DevState& S, const int32_t* gate, cudaStream_t st,
-                       Recorder* rec) {
-  const size_t n16 = (size_t)P.NLU * S.Bp * sizeof(T) / 16;  // NLU*Bp*sizeof(T) is a multiple of 128
+                       Recorder* rec, bool whole) {
+  // per tile, NLU * 32 values; the sparse segments are the first NS * 32
+  // (both multiples of 128 bytes).  The dense block is left alone unless
+  // `whole`: the Schur tasks then write every position of it.
+  const size_t stride16 = (size_t)P.NLU * kTile * sizeof(T) / 16;
+  const size_t n16 = (whole || P.nd == 0) ? stride16 : (size_t)P.NS * kTile * sizeof(T) / 16;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  NRPF_LAUNCH(rec, K_ZERO, st, k_zero16<<<sms * 8, 256, 0, st>>>(reinterpret_cast<uint4*>(S.lu), n16, gate));
+  NRPF_LAUNCH(rec, K_ZERO, st,
+              k_zero16<<<sms * 8, 256, 0, st>>>(reinterpret_cast<uint4*>(S.lu), n16, stride16, S.Bp / kTile, gate));
   if (P.n_one > 0)
     NRPF_LAUNCH(rec, K_ONES, st, k_set_ones<T><<<dim3(1, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate));
 }
@@ -1154,7 +1175,7 @@ void launch_lu_out(const DevPlan& P, const DevState& S, int B, const int64_t* ma
   template void launch_mismatch<T>(const DevPlan&, const DevState&, int, const int32_t*, cudaStream_t,       \
                                    Recorder*);                                                               \
   template void launch_prepare_lu<T>(const DevPlan&, const DevState&, const int32_t*, cudaStream_t,          \
-                                     Recorder*);                                                             \
+                                     Recorder*, bool);                                                       \
   template void launch_factor<T>(const DevPlan&, const DevState&, const std::vector<int32_t>&,               \
                                  const int32_t*, cudaStream_t, Recorder*);                                   \
   template void launch_solve<T>(const DevPlan&, const DevState&, const std::vector<int32_t>&,                \

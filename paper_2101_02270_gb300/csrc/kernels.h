@@ -46,8 +46,11 @@ template <typename T>
 void launch_mismatch(const DevPlan& P, const DevState& S, int jac, const int32_t* gate, cudaStream_t st,
                      Recorder* rec = nullptr);
 template <typename T>
+// Zero the LU workspace (whole = false: only the sparse segments; the
+// refactorisation then writes every position of the dense block) and set the
+// identity padding of the dense block.
 void launch_prepare_lu(const DevPlan& P, const DevState& S, const int32_t* gate, cudaStream_t st,
-                       Recorder* rec = nullptr);
+                       Recorder* rec = nullptr, bool whole = true);
 template <typename T>
 void launch_factor(const DevPlan& P, const DevState& S, const std::vector<int32_t>& lvl_ptr,
                    const int32_t* gate, cudaStream_t st, Recorder* rec = nullptr);

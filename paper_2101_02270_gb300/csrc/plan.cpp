@@ -186,6 +186,7 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
       for (int t = 0; t < 4; ++t) P.nnz_j += jm[t] >= 0;
     }
   P.one_pos.clear();
+  // (the Schur tasks' Jacobian-row masks are filled after the tasks exist)
   for (int t = P.nd; t < P.ndp; ++t) P.one_pos.push_back((int32_t)(P.NS + (int64_t)t * P.ndp + t));
   P.rhs_pos_p.assign(n, -1);
   P.rhs_pos_q.assign(n, -1);
@@ -202,7 +203,7 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
   double fma = 0;
   for (int k = 0; k < s; ++k)
     if (!std::is_sorted(Lpat[k].begin(), Lpat[k].end())) { err = "internal: L pattern not sorted"; return NRPF_ERR_PATTERN; }
-  P.schur_task.clear(); P.schur_ent.clear(); P.schur_u.clear(); P.schur_mask.clear();
+  P.schur_task.clear(); P.schur_ent.clear(); P.schur_u.clear(); P.schur_jmask.clear();
   for (int j = 0; j < m; ++j) {
     int lv = 0;
     for (int k : Ustr[j]) {  // k < s, ascending
@@ -230,10 +231,9 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
       P.upd.push_back(u);
     }
     if (j >= s && P.nd > 0) {
-      const int nch = (P.nd + 31) / 32;
+      const int nch = (P.ndp + 31) / 32;
       for (int c = 0; c < nch; ++c) {
         const int e0 = (int)P.schur_ent.size();
-        uint32_t mask = 0;
         for (int k : Ustr[j]) {
           const int32_t ukj = (int32_t)P.pos(k, j);
           auto it = std::lower_bound(Lpat[k].begin(), Lpat[k].end(), s + 32 * c);
@@ -243,14 +243,11 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
             const int r = *it - s - 32 * c;
             P.schur_ent.push_back((int32_t)((lpos << 5) | r));
             P.schur_u.push_back(ukj);
-            mask |= 1u << r;
           }
         }
-        if ((int)P.schur_ent.size() > e0) {
-          if (P.schur_ent.size() >= ((size_t)1 << 31)) { err = "Schur task list exceeds 2^31 entries"; return NRPF_ERR_NOMEM; }
-          P.schur_task.insert(P.schur_task.end(), {j - s, c, e0, (int32_t)P.schur_ent.size()});
-          P.schur_mask.push_back(mask);
-        }
+        if (P.schur_ent.size() >= ((size_t)1 << 31)) { err = "Schur task list exceeds 2^31 entries"; return NRPF_ERR_NOMEM; }
+        P.schur_task.insert(P.schur_task.end(), {j - s, c, e0, (int32_t)P.schur_ent.size()});
+        P.schur_jmask.push_back(0u);
       }
     }
     level[j] = lv;
@@ -267,6 +264,16 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
     for (int j = 0; j < m; ++j)
       if (level[j] == l && (j < s || P.col_upd_ptr[j + 1] > P.col_upd_ptr[j])) P.lu_lvl_cols.push_back(j);
     P.lu_lvl_ptr[l + 1] = (int32_t)P.lu_lvl_cols.size();
+  }
+  // rows of each Schur task's chunk that hold a Jacobian entry
+  if (P.nd > 0) {
+    const int nch = (P.ndp + 31) / 32;
+    for (int32_t q : P.jmap) {
+      if (q < P.NS) continue;
+      const int64_t d = q - P.NS;
+      const int col = (int)(d / P.ndp), row = (int)(d % P.ndp);
+      P.schur_jmask[(size_t)col * nch + row / 32] |= 1u << (row % 32);
+    }
   }
   for (int j = 0; j < s; ++j) fma += (double)(P.ce[j] - P.dp[j] - 1);  // normalisation
   for (int k = 0; k < P.ndp; ++k) {

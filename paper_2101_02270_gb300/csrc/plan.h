@@ -49,11 +49,13 @@ struct HostPlan {
   // The updates of a dense column j by sparse columns k keep only their rows
   // < s in the level schedule (they finish U(k, j)); the rows >= s are applied
   // afterwards, all dense columns at once, by tasks of (dense column, chunk of
-  // 32 dense rows): schur_task[4t..] = {j - s, chunk, first entry, end};
+  // 32 dense rows), one per chunk of every real dense column, in that order:
+  // schur_task[4t..] = {j - s, chunk, first entry, end};
   // entry e: schur_ent[e] = (position of L(i, k) << 5) | (i - s - 32 chunk),
-  // schur_u[e] = position of U(k, j).
+  // schur_u[e] = position of U(k, j).  A task writes every row of its chunk
+  // (below the padded size): the row's Jacobian value, or 0, minus its sum.
   std::vector<int32_t> schur_task, schur_ent, schur_u;
-  std::vector<uint32_t> schur_mask;  // [tasks] rows of the chunk that receive updates
+  std::vector<uint32_t> schur_jmask;  // [tasks] rows of the chunk holding a Jacobian entry
   // ---- forward / backward substitution schedules (row-oriented) ----
   std::vector<int32_t> fw_lvl_ptr, fw_rows, fw_ptr, fw_pos, fw_col;
   std::vector<int32_t> bw_lvl_ptr, bw_rows, bw_ptr, bw_pos, bw_col;
