@@ -136,7 +136,7 @@ def _oracle_cases(task):
     return st
 
 
-def oracle_sample(g, S, V0, seconds, cores, ins=None):
+def oracle_sample(g, S, V0, seconds, cores, ins=None, gpu=None):
     """Time the CPU oracle on a bounded sample of the workload: a first
     calibration run sizes the sample to about `seconds` of work on `cores`
     processes.  ins [B, nbr] (optional): per-instance branch sets, each
@@ -168,9 +168,26 @@ def oracle_sample(g, S, V0, seconds, cores, ins=None):
     dt = time.perf_counter() - t0
     conv = int(np.sum(st == 0))
     what = "instances (own admittance matrix each)" if ins is not None else "scenarios"
-    return {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {size} of {B} {what}, scipy SuperLU per Newton step, "
-                      f"{cores} spawn processes, {dt:.1f} s"}
+    out = {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"first {size} of {B} {what}, scipy SuperLU per Newton step, "
+                     f"{cores} spawn processes, {dt:.1f} s"}
+    if gpu is not None:
+        # the GPU's results on (the first few of) the same instances against
+        # the oracle's, solved again one by one with their voltages kept
+        Vg, itg, stg = gpu
+        k = min(size, 8)
+        Y = None if ins is not None else nrpf.make_ybus(g.n, g.f, g.t, g.r, g.x, g.b)
+        dv, dit, same = 0.0, 0, True
+        for b in range(k):
+            Yb = Y if Y is not None else nrpf.make_ybus(g.n, g.f[ins[b]], g.t[ins[b]], g.r[ins[b]], g.x[ins[b]],
+                                                        g.b[ins[b]])
+            Vo, ito, sto = nrpf.newton(Yb, S[b], V0[b], g.bus_type, TOL, MAXIT)
+            same = same and int(stg[b]) == int(sto)
+            if sto == 0:
+                dv = max(dv, float(np.max(np.abs(Vg[b] - Vo))))
+                dit = max(dit, abs(int(itg[b]) - int(ito)))
+        out["vs_oracle"] = {"instances": k, "same_status": same, "max_abs_dv": dv, "max_iter_diff": dit}
+    return out
 
 
 def run_reference(args):
@@ -790,7 +807,8 @@ def run_ours(args):
                                "case": "every single-branch outage that keeps the grid connected, per-instance "
                                        "admittances on the base pattern, one injection profile per load level"})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1, ins)
+        line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1, ins,
+                                             gpu=(out[0].cpu().numpy(), iters, status))
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -247,11 +247,8 @@ int enqueue_solve(pf_plan* p, int B, const double* ybus, const double* sbus, con
     }
   }
   // the last convergence test (iteration ctl->it; nothing is active after an
-  // early exit)
-  if (P.m > 0) {
-    nrpf::launch_prepare_lu<T>(P, S, nrpf::ctl_prev(S), st, rec);
-    nrpf::launch_mismatch<T>(P, S, 1, nrpf::ctl_prev(S), st, rec);
-  }
+  // early exit): the mismatch only, no Jacobian
+  if (P.m > 0) nrpf::launch_mismatch<T>(P, S, 0, nrpf::ctl_prev(S), st, rec);
   nrpf::launch_check(S, st, rec);
   nrpf::launch_store(P, S, B, v_out, iters, status, st, rec);
   return NRPF_OK;
