@@ -181,6 +181,18 @@ int pf_ybus_values(int n, int nbr, const int32_t* f, const int32_t* t, const dou
                    const double* b, int B, const uint8_t* in_service, const int32_t* rowptr,
                    const int32_t* colidx, double* y);
 
+/* Batched Newton-Raphson on the host cores (the paper's CPU solver: SIMD
+ * across instances, threads across mini-batches, Sec. 4).  Same plan, same
+ * arithmetic and conventions as pf_solve_batch in FP64 (up to summation
+ * order): instances in mini-batches of 8 interleaved lanes, left-looking
+ * sparse refactor in column order, the sparse columns' updates of the dense
+ * block, dense LU of the trailing block, FS/BS, polar update.
+ * host in : sbus / v0 [B, n] complex; host out: v_out [B, n], iters [B],
+ * status [B].  threads: host threads (0 = all hardware threads).  Works on
+ * host-only plans.  Synchronous.  Errors: NRPF_ERR_ARG. */
+int pf_solve_batch_cpu(pf_plan* p, int B, const double* sbus, const double* v0, double tol, int maxit,
+                       double* v_out, int32_t* iters, uint8_t* status, int threads);
+
 /* Second chance for failed instances (Sec. 3.2: cases whose refactorisation
  * without pivoting breaks down are solved again with a pivoting
  * factorisation).  Newton-Raphson on the host cores with a left-looking

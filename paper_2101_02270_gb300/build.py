@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cu", "kernels.cu", "mlp.cu", "multi.cu", "noalloc.cu", "peak.cu", "flows.cu", "plan.cpp",
-           "ordering.cpp", "retry.cpp"]
+           "ordering.cpp", "retry.cpp",
+           "cpu_batch.cpp"]
 
 
 def _nvcc() -> str:
@@ -30,8 +31,11 @@ def _nvcc() -> str:
 
 def _compile(src: str, nvcc: str, extra: list[str]) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+    # host code at -O3: the batched host solver relies on the compiler's
+    # vectoriser for its loops over instance lanes (no target-specific flags)
+    host_opt = "-O3" if src.endswith(".cpp") else "-O2"
     cmd = [nvcc, "-c", os.path.join(CSRC, src), "-o", obj, "-O3", "-std=c++17", "-lineinfo",
-           "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", *ARCH, *extra]
+           "-Xcompiler", "-fPIC", "-Xcompiler", host_opt, *ARCH, *extra]
     subprocess.run(cmd, check=True)
     return obj
 

@@ -146,6 +146,23 @@ class Plan:
                                          _lib._np_ptr(v), _lib._np_ptr(it), _lib._np_ptr(st)), "pf_solve_pivoting_host")
         return v, it, st
 
+    def solve_cpu(self, sbus: np.ndarray, v0: np.ndarray, tol: float = 1e-8, maxit: int = 10, threads: int = 0):
+        """Batched Newton-Raphson on the host cores (pf_solve_batch_cpu): numpy
+        complex128 [B, n] in, numpy (v, iters, status) out.  Works on host-only
+        plans."""
+        S = np.ascontiguousarray(sbus, np.complex128)
+        V0 = np.ascontiguousarray(v0, np.complex128)
+        B = S.shape[0]
+        if S.shape != (B, self.n) or V0.shape != (B, self.n):
+            raise ValueError(f"expected complex128 [{B}, {self.n}]")
+        v = np.empty_like(S)
+        it = np.empty(B, np.int32)
+        st = np.empty(B, np.uint8)
+        check(lib.pf_solve_batch_cpu(self._h, B, _lib._np_ptr(S), _lib._np_ptr(V0), float(tol), int(maxit),
+                                     _lib._np_ptr(v), _lib._np_ptr(it), _lib._np_ptr(st), int(threads)),
+              "pf_solve_batch_cpu")
+        return v, it, st
+
     def retry_failed(self, sbus: torch.Tensor, v0: torch.Tensor, out, tol: float = 1e-8, maxit: int = 10) -> int:
         """Second chance (pf_retry_failed): re-solve with the pivoting host
         solver every instance of a finished solve (device arrays sbus, v0 and
