@@ -190,6 +190,21 @@ def oracle_sample(g, S, V0, seconds, cores, ins=None, gpu=None):
     return out
 
 
+def whole_solve_roofline(parts, ms_per_step, kernel):
+    """HBM roofline of a solve done by one persistent kernel: algorithmic
+    bytes per instance-iteration (LU values written and read once, voltages,
+    injections, right-hand side and solution: 2 w nnz_LU + 8 (8 n + 4 m)),
+    summed over (plan info, LU bytes per value w, Newton updates of its
+    instances), over the step time, against the measured copy bandwidth."""
+    hbm, kind = measured_hbm()
+    total = sum((2 * w * info["nnz_lu"] + 8 * (8 * info["n"] + 4 * info["m"])) * int(upd)
+                for info, w, upd in parts)
+    achieved = total / (ms_per_step / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_kind": f"{kind} HBM copy bandwidth",
+            "bytes_per_step": total}
+
+
 def cpu_batched_sample(pf, g, S, V0, seconds):
     """The library's batched host solver (pf_solve_batch_cpu: instances in
     SIMD lanes, all hardware threads) on a bounded sample of the workload, a
@@ -402,6 +417,12 @@ def run_feeders(args):
     torch.cuda.synchronize()
     e2e = int(np.sum(st_h.numpy() == 0)) * args.steps / (e0.elapsed_time(e1) / 1e3)
     nbus = np.array([g.n for g in fs])
+    w = 4 if lu == "fp32" else 8
+    parts, off = [], 0
+    for p_, sc in zip(plans, scen):
+        parts.append((p_.info, w, int(it[off:off + sc.batch].sum())))
+        off += sc.batch
+    roof = whole_solve_roofline(parts, ms / args.steps, "k_multi (the whole persistent solve)")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -417,7 +438,15 @@ def run_feeders(args):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(2 * S.nbytes),
                 "d2h_bytes_per_step": int(S.nbytes + 5 * mp.total)},
         "gpu_launches": 1,
+        "roofline": roof,
     }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on every 64th feeder's scenarios, the seconds shared out
+        picks = list(range(0, len(fs), 64))
+        res = [oracle_sample(fs[i], scen[i].sbus(fs[i]), scen[i].v0_flat(fs[i]), args.cpu_seconds / len(picks),
+                             os.cpu_count() or 1) for i in picks]
+        line["cpu_baseline"] = dict(res[-1], value=float(np.mean([r["value"] for r in res])),
+                                    sample=f"feeders {picks}, each: " + res[-1]["sample"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     mp.close()
@@ -558,7 +587,12 @@ def run_warmstart(args):
         "clocks": clk, "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * S_pin.nbytes),
                 "d2h_bytes_per_step": int(v_pin.nbytes + it_pin.nbytes + st_pin.nbytes)},
+        "roofline": whole_solve_roofline([(plan64.info, 8, int(itw.sum()))], ms_warm64,
+                                         "the warm-started FP64 solve (its dense update is FP64-bound)"),
     }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1)
+        line["cpu_baseline"]["sample"] += " (flat start: the oracle has no network)"
     print(json.dumps(line), flush=True)
 
 
@@ -631,7 +665,11 @@ def run_small(args):
         "clocks": clk, "e2e": {"value": conv / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(2 * S_h.nbytes),
                                "d2h_bytes_per_step": int(S_h.nbytes)},
         "gpu_launches": 1,
+        "roofline": whole_solve_roofline([(plan.info, 8 if args.lu == "fp64" else 4, int(it.sum()))], ms,
+                                         "k_multi (the whole persistent solve)"),
     }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1)
     print(json.dumps(line), flush=True)
 
 
