@@ -85,12 +85,15 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_multi(DevMulti M, const doub
         s = sbus[base + i];
         v = v0[base + i];
       }
-      const double mag = sqrt(v.x * v.x + v.y * v.y);
+      // a start on the positive real axis (flat start) needs no FP64 sqrt
+      // or atan2
+      const bool real = v.y == 0.0 && v.x > 0.0;
+      const double mag = real ? v.x : sqrt(v.x * v.x + v.y * v.y);
       const int o = i * kTile + lane;
       psp[o] = s.x;
       qsp[o] = s.y;
       vm[o] = mag;
-      va[o] = atan2(v.y, v.x);
+      va[o] = real ? 0.0 : atan2(v.y, v.x);
       ve[o] = v.x;
       vf[o] = v.y;
       vinv[o] = 1.0 / mag;
@@ -118,12 +121,14 @@ __global__ void __launch_bounds__(32 * kMaxWarps) k_multi(DevMulti M, const doub
           if (k != i) {
             const int4 jm = reinterpret_cast<const int4*>(P.jmap)[d];
             if (jm.x >= 0) {
-              const double Wr = ei * yr + fi * yi, Wi = fi * yr - ei * yi;
-              const double ik = vinv[k * kTile + lane];
-              LU[(size_t)jm.x * kTile + lane] = (T)Wi;
-              if (jm.y >= 0) LU[(size_t)jm.y * kTile + lane] = (T)(Wr * ik);
-              if (jm.z >= 0) LU[(size_t)jm.z * kTile + lane] = (T)(-Wr);
-              if (jm.w >= 0) LU[(size_t)jm.w * kTile + lane] = (T)(Wi * ik);
+              // off-diagonal Jacobian entries in the LU precision (stored in
+              // it); the mismatch stays FP64
+              const T Wr = (T)ei * (T)yr + (T)fi * (T)yi, Wi = (T)fi * (T)yr - (T)ei * (T)yi;
+              const T ik = (T)vinv[k * kTile + lane];
+              LU[(size_t)jm.x * kTile + lane] = Wi;
+              if (jm.y >= 0) LU[(size_t)jm.y * kTile + lane] = Wr * ik;
+              if (jm.z >= 0) LU[(size_t)jm.z * kTile + lane] = -Wr;
+              if (jm.w >= 0) LU[(size_t)jm.w * kTile + lane] = Wi * ik;
             }
           }
         }
