@@ -706,8 +706,10 @@ def run_ours(args):
     plan = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision=args.lu,
                                  dense_frac=args.dense_frac, panel=args.panel, max_batch=B)
     plan_ms = 1e3 * (time.perf_counter() - t0)
-    Y_np = plan.ybus_values(ins) if n1 else None
-    Yd = torch.from_numpy(Y_np).to(dev) if n1 else None
+    # N-1: each instance lists its outaged branch; the admittances are built
+    # on the device from the plan's base values
+    out_np = np.argmin(ins, axis=1).astype(np.int32)[:, None] if n1 else None
+    Od = torch.from_numpy(out_np).to(dev) if n1 else None
     info = plan.info
     fp64_peak, fp32_peak = pf._lib.fma_peak(C.c_void_p(torch.cuda.current_stream().cuda_stream))
     out = (torch.empty((B, g.n), dtype=torch.complex128, device=dev),
@@ -716,7 +718,7 @@ def run_ours(args):
 
     def step():
         if n1:
-            return plan.solve_y(Yd, S, V0, TOL, args.maxit, out=out)
+            return plan.solve_outages(Od, S, V0, TOL, args.maxit, out=out)
         return plan.solve(S, V0, TOL, args.maxit, out=out)
 
     for _ in range(max(args.warmup, 0)):
@@ -767,15 +769,15 @@ def run_ours(args):
     it_h = torch.empty(B, dtype=torch.int32).pin_memory()
     st_h = torch.empty(B, dtype=torch.uint8).pin_memory()
     if n1:
-        # per-instance admittances travel too: copies in, solve, copies out
-        Y_h = torch.from_numpy(Y_np).pin_memory()
-        Sd, Vd, Ydd = torch.empty_like(S), torch.empty_like(V0), torch.empty_like(Yd)
+        # the outage lists travel with the injections: copies in, solve, copies out
+        O_h = torch.from_numpy(out_np).pin_memory()
+        Sd, Vd, Odd = torch.empty_like(S), torch.empty_like(V0), torch.empty_like(Od)
 
         def e2e_step():
-            Ydd.copy_(Y_h, non_blocking=True)
+            Odd.copy_(O_h, non_blocking=True)
             Sd.copy_(S_h, non_blocking=True)
             Vd.copy_(V0_h, non_blocking=True)
-            v, it, st = plan.solve_y(Ydd, Sd, Vd, TOL, args.maxit, out=out)
+            v, it, st = plan.solve_outages(Odd, Sd, Vd, TOL, args.maxit, out=out)
             V_h.copy_(v, non_blocking=True)
             it_h.copy_(it, non_blocking=True)
             st_h.copy_(st, non_blocking=True)
@@ -791,7 +793,7 @@ def run_ours(args):
     barrier()
     ms_e2e, conv_e2e = combine_ranks(e0.elapsed_time(e1), int(np.sum(st_h.numpy() == 0)), dev)
     e2e_value = conv_e2e * args.steps / (ms_e2e / 1e3)
-    h2d = 2 * B * g.n * 16 + (Y_np.nbytes if n1 else 0)
+    h2d = 2 * B * g.n * 16 + (out_np.nbytes if n1 else 0)
     d2h = B * g.n * 16 + B * 4 + B
 
     # ---- roofline of the dominant kernel (dense trailing update) ----
@@ -856,7 +858,7 @@ def run_ours(args):
         "kernel_ms": {k: round(v[2], 3) for k, v in prof.items() if v[1] > 0},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "api": ("pf_solve_batch_y after page-locked host copies of the admittances and injections" if n1
+                "api": ("pf_solve_batch_outages after page-locked host copies of the outage lists and injections" if n1
                         else "pf_solve_batch_host (page-locked host buffers, copies overlapped across calls)")},
         "gpu_launches": launches,
     }
@@ -864,7 +866,8 @@ def run_ours(args):
         line["config"].update({"contingencies": int(B // len(gridgen.N1_LEVELS)),
                                "load_levels": list(gridgen.N1_LEVELS),
                                "case": "every single-branch outage that keeps the grid connected, per-instance "
-                                       "admittances on the base pattern, one injection profile per load level"})
+                                       "admittances built on the device from the base values and the outaged "
+                                       "branch (pf_solve_batch_outages), one injection profile per load level"})
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1, ins,
                                              gpu=(out[0].cpu().numpy(), iters, status))

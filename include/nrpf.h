@@ -168,6 +168,23 @@ int pf_solve_batch(pf_plan* p, int B, const double* sbus, const double* v0, doub
 int pf_solve_batch_y(pf_plan* p, int B, const double* ybus, const double* sbus, const double* v0, double tol,
                      int maxit, double* v_out, int32_t* iters, uint8_t* status, void* stream);
 
+/* Branch outages on the device (static N-1 / N-k analysis without building
+ * admittance arrays on the host).  pf_plan_set_branches keeps the branch
+ * data of the plan's grid (pi model, as pf_ybus_from_branches; every branch
+ * must have its entries in the plan's pattern); pf_solve_batch_outages then
+ * solves B instances whose admittances are the plan's base values minus the
+ * stamps of their outaged branches, built on the device.
+ * pf_plan_set_branches: host in nbr, f/t/r/x/b [nbr].  Errors: NRPF_ERR_ARG,
+ * NRPF_ERR_PATTERN (a branch entry missing from the pattern), NRPF_ERR_NOMEM.
+ * pf_solve_batch_outages: device in outages [B, k] branch indices (-1 = none;
+ * repeated indices are removed once), sbus / v0 [B, n]; device out as
+ * pf_solve_batch.  Errors: as pf_solve_batch; NRPF_ERR_ARG also when no
+ * branches were set or k < 0. */
+int pf_plan_set_branches(pf_plan* p, int nbr, const int32_t* f, const int32_t* t, const double* r, const double* x,
+                         const double* b);
+int pf_solve_batch_outages(pf_plan* p, int B, const int32_t* outages, int k, const double* sbus, const double* v0,
+                           double tol, int maxit, double* v_out, int32_t* iters, uint8_t* status, void* stream);
+
 /* Host helper for pf_solve_batch_y: Ybus values of B branch-status cases on a
  * given pattern (MATPOWER pi model as pf_ybus_from_branches; branches out of
  * service contribute nothing).

@@ -46,7 +46,7 @@ class pf_profile(C.Structure):
 
 
 EXPORTS = ["pf_options_default", "pf_ybus_from_branches", "pf_plan_create", "pf_plan_get_info",
-           "pf_plan_get_pattern", "pf_solve_batch", "pf_solve_batch_host", "pf_solve_batch_y", "pf_ybus_values", "pf_branch_flows", "pf_solve_pivoting_host", "pf_retry_failed", "pf_solve_batch_cpu", "pf_stage_mismatch", "pf_stage_factor",
+           "pf_plan_get_pattern", "pf_solve_batch", "pf_solve_batch_host", "pf_solve_batch_y", "pf_ybus_values", "pf_plan_set_branches", "pf_solve_batch_outages", "pf_branch_flows", "pf_solve_pivoting_host", "pf_retry_failed", "pf_solve_batch_cpu", "pf_stage_mismatch", "pf_stage_factor",
            "pf_stage_linear_solve", "pf_profile_start", "pf_profile_read", "pf_kernel_class_name",
            "pf_fma_peak", "pf_stage_mismatch_noalloc", "pf_multi_create", "pf_multi_solve",
            "pf_multi_set_config", "pf_multi_get_config", "pf_multi_autotune", "pf_multi_destroy",
@@ -72,6 +72,8 @@ def _load():
     lib.pf_solve_batch_host.argtypes = [P, I, P, P, D, I, P, P, P, I, P]
     lib.pf_solve_batch_y.argtypes = [P, I, P, P, P, D, I, P, P, P, P]
     lib.pf_ybus_values.argtypes = [I, I, P, P, P, P, P, I, P, P, P, P]
+    lib.pf_plan_set_branches.argtypes = [P, I, P, P, P, P, P]
+    lib.pf_solve_batch_outages.argtypes = [P, I, P, I, P, P, D, I, P, P, P, P]
     lib.pf_branch_flows.argtypes = [I, I, P, P, P, P, P, I, P, P, P, P, P]
     lib.pf_solve_pivoting_host.argtypes = [P, I, P, P, D, I, P, P, P]
     lib.pf_solve_batch_cpu.argtypes = [P, I, P, P, D, I, P, P, P, I]

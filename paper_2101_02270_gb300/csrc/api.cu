@@ -206,21 +206,27 @@ int ensure_yv(pf_plan* p) {
   return NRPF_OK;
 }
 
-// ybus: per-instance [B, nnzY] complex device values, or null for the plan's
+// ybus: per-instance [B, nnzY] complex device values, or null for the plan's;
+// outages (device [B, k], with ybus null): per-instance admittances built on
+// the device from the plan's base values and branch stamps
 template <typename T>
 int enqueue_solve(pf_plan* p, int B, const double* ybus, const double* sbus, const double* v0, double tol,
-                  int maxit, double* v_out, int32_t* iters, uint8_t* status, cudaStream_t st) {
+                  int maxit, double* v_out, int32_t* iters, uint8_t* status, cudaStream_t st,
+                  const int32_t* outages = nullptr, int k = 0) {
   const DevPlan& P = p->dp;
   // grids cover this batch's tiles only (tiles are contiguous per array, so
   // the first Bp of the workspace's capacity serve)
   DevState S = p->st;
   S.Bp = (B + kTile - 1) / kTile * kTile;
   nrpf::Recorder* rec = &p->rec;
-  if (ybus) {
+  if (ybus || outages) {
     int rc = ensure_yv(p);
     if (rc) return rc;
     S.yv = reinterpret_cast<const double2*>(p->yv_mem);
-    nrpf::launch_load_y(P, S, B, ybus, st, rec);
+    if (ybus)
+      nrpf::launch_load_y(P, S, B, ybus, st, rec);
+    else
+      nrpf::launch_outage_y(P, S, B, outages, k, p->d_bpos, p->d_bval, p->nbr, st, rec);
   }
   nrpf::launch_load(P, S, B, sbus, v0, st, rec);
   nrpf::launch_ctl_init(S, maxit, tol, st, rec);
@@ -514,6 +520,62 @@ int pf_solve_batch_y(pf_plan* p, int B, const double* ybus, const double* sbus, 
   return check_launch();
 }
 
+int pf_plan_set_branches(pf_plan* p, int nbr, const int32_t* f, const int32_t* t, const double* r, const double* x,
+                         const double* b) {
+  if (!p || p->host_only || nbr < 0 || (nbr > 0 && (!f || !t || !r || !x || !b))) return NRPF_ERR_ARG;
+  const HostPlan& h = p->hp;
+  auto find = [&](int i, int k) -> int {
+    const int32_t* lo = h.colidx.data() + h.rowptr[i];
+    const int32_t* hi = h.colidx.data() + h.rowptr[i + 1];
+    const int32_t* q = std::lower_bound(lo, hi, k);
+    return (q != hi && *q == k) ? (int)(q - h.colidx.data()) : -1;
+  };
+  std::vector<int4> pos(nbr);
+  std::vector<double> val((size_t)nbr * 3);
+  for (int e = 0; e < nbr; ++e) {
+    const int a = f[e], c = t[e];
+    if (a < 0 || a >= h.n || c < 0 || c >= h.n) return NRPF_ERR_ARG;
+    const double den = r[e] * r[e] + x[e] * x[e];
+    if (!(den > 0.0) || !std::isfinite(den) || !std::isfinite(b[e])) return NRPF_ERR_ARG;
+    pos[e] = make_int4(find(a, a), find(c, c), find(a, c), find(c, a));
+    if (pos[e].x < 0 || pos[e].y < 0 || pos[e].z < 0 || pos[e].w < 0) return NRPF_ERR_PATTERN;
+    val[3 * e] = r[e] / den;
+    val[3 * e + 1] = -x[e] / den;
+    val[3 * e + 2] = 0.5 * b[e];
+  }
+  CK(cudaDeviceSynchronize());
+  if (p->d_bpos) cudaFree(p->d_bpos);
+  if (p->d_bval) cudaFree(p->d_bval);
+  p->d_bpos = nullptr;
+  p->d_bval = nullptr;
+  p->nbr = 0;
+  CK(cudaMalloc(&p->d_bpos, std::max<size_t>(pos.size() * sizeof(int4), 16)));
+  CK(cudaMalloc(&p->d_bval, std::max<size_t>(val.size() * sizeof(double), 16)));
+  if (nbr > 0) {
+    CK(cudaMemcpy(p->d_bpos, pos.data(), pos.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->d_bval, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  p->nbr = nbr;
+  return NRPF_OK;
+}
+
+int pf_solve_batch_outages(pf_plan* p, int B, const int32_t* outages, int k, const double* sbus, const double* v0,
+                           double tol, int maxit, double* v_out, int32_t* iters, uint8_t* status, void* stream) {
+  if (!p || p->host_only || B < 0 || k < 0 || maxit < 0 || !std::isfinite(tol) || tol < 0 || !p->d_bpos)
+    return NRPF_ERR_ARG;
+  if (B == 0) return NRPF_OK;
+  if ((k > 0 && !outages) || !sbus || !v0 || !v_out || !iters || !status) return NRPF_ERR_ARG;
+  int rc = ensure_capacity(p, B);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (p->lu_precision == NRPF_LU_FP32)
+    rc = enqueue_solve<float>(p, B, nullptr, sbus, v0, tol, maxit, v_out, iters, status, st, outages, k);
+  else
+    rc = enqueue_solve<double>(p, B, nullptr, sbus, v0, tol, maxit, v_out, iters, status, st, outages, k);
+  if (rc) return rc;
+  return check_launch();
+}
+
 int pf_ybus_values(int n, int nbr, const int32_t* f, const int32_t* t, const double* r, const double* x,
                    const double* b, int B, const uint8_t* in_service, const int32_t* rowptr,
                    const int32_t* colidx, double* y) {
@@ -756,6 +818,8 @@ void pf_plan_destroy(pf_plan* p) {
   free_ws(p);
   if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
   if (p->yv_mem) cudaFree(p->yv_mem);
+  if (p->d_bpos) cudaFree(p->d_bpos);
+  if (p->d_bval) cudaFree(p->d_bval);
   for (int i = 0; i < 2; ++i) {
     if (p->stage_mem[i]) cudaFree(p->stage_mem[i]);
     if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);

@@ -44,6 +44,12 @@ struct pf_plan {
   cudaEvent_t ev_done[2] = {nullptr, nullptr};   // slot's chunk solved
   cudaEvent_t ev_out[2] = {nullptr, nullptr};    // slot's results copied out
   void* yv_mem = nullptr;  // per-instance Ybus values, capacity x nnzY complex
+  // branch stamps for device-built outage cases: per branch the pattern
+  // positions of (f,f), (t,t), (f,t), (t,f) and (series G, series B, half
+  // charging)
+  int nbr = 0;
+  int4* d_bpos = nullptr;
+  double* d_bval = nullptr;  // [nbr * 3]
   int yv_cap = 0;
   int slot_next = 0;                            // staging slot of the next chunk
   bool slot_used[2] = {false, false};           // slot holds a chunk whose copy-out was enqueued

@@ -256,6 +256,42 @@ __global__ void k_load_y(int nnzY, int B, const double2* __restrict__ y, double2
   }
 }
 
+// Outage cases built on the device: every instance starts from the plan's
+// base admittances (interleaved layout), then loses the stamps of its outaged
+// branches (repeated indices of one instance count once).
+__global__ void k_base_y(DevPlan P, double2* __restrict__ yv, int tiles) {
+  const int lane = threadIdx.x;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;  // (tile, entry)
+  if (q >= (int64_t)tiles * P.nnzY) return;
+  const int d = (int)(q % P.nnzY);
+  yv[q * kTile + lane] = make_double2(P.yre[d], P.yim[d]);
+}
+
+__global__ void k_outage_y(int nnzY, int B, int k, const int32_t* __restrict__ outages,
+                           const int4* __restrict__ bpos, const double* __restrict__ bval, int nbr,
+                           double2* __restrict__ yv) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double2* y = yv + (size_t)(b / kTile) * nnzY * kTile + (b % kTile);
+  for (int a = 0; a < k; ++a) {
+    const int e = outages[(size_t)b * k + a];
+    if (e < 0 || e >= nbr) continue;
+    bool seen = false;
+    for (int c = 0; c < a; ++c) seen = seen || outages[(size_t)b * k + c] == e;
+    if (seen) continue;
+    const int4 ps = bpos[e];
+    const double gs = bval[3 * e], bs = bval[3 * e + 1], bh = bval[3 * e + 2];
+    y[(size_t)ps.x * kTile].x -= gs;
+    y[(size_t)ps.x * kTile].y -= bs + bh;
+    y[(size_t)ps.y * kTile].x -= gs;
+    y[(size_t)ps.y * kTile].y -= bs + bh;
+    y[(size_t)ps.z * kTile].x += gs;
+    y[(size_t)ps.z * kTile].y += bs;
+    y[(size_t)ps.w * kTile].x += gs;
+    y[(size_t)ps.w * kTile].y += bs;
+  }
+}
+
 // Convergence test and per-instance bookkeeping, one thread per instance.
 // it = number of updates performed so far.
 __global__ void k_check(DevState S, int Bp) {
@@ -995,6 +1031,17 @@ void launch_load_y(const DevPlan& P, const DevState& S, int B, const double* y, 
   NRPF_LAUNCH(rec, K_LOAD, st,
               k_load_y<<<g, dim3(32, 8), 0, st>>>(P.nnzY, B, reinterpret_cast<const double2*>(y),
                                                   const_cast<double2*>(S.yv)));
+}
+
+void launch_outage_y(const DevPlan& P, const DevState& S, int B, const int32_t* outages, int k, const int4* bpos,
+                     const double* bval, int nbr, cudaStream_t st, Recorder* rec) {
+  const int tiles = S.Bp / kTile;
+  double2* yv = const_cast<double2*>(S.yv);
+  NRPF_LAUNCH(rec, K_LOAD, st,
+              k_base_y<<<grid2((int64_t)tiles * P.nnzY, 8, 1), dim3(32, 8), 0, st>>>(P, yv, tiles));
+  if (k > 0)
+    NRPF_LAUNCH(rec, K_LOAD, st,
+                k_outage_y<<<(B + 127) / 128, 128, 0, st>>>(P.nnzY, B, k, outages, bpos, bval, nbr, yv));
 }
 
 void launch_ctl_init(const DevState& S, int maxit, double tol, cudaStream_t st, Recorder* rec) {

@@ -31,6 +31,11 @@ inline const int32_t* ctl_cur(const DevState& S) {
 void launch_load_y(const DevPlan& P, const DevState& S, int B, const double* y, cudaStream_t st,
                    Recorder* rec = nullptr);
 
+// Per-instance Ybus values of outage cases into S.yv: the plan's base values
+// minus the stamps of each instance's outaged branches (outages [B, k]).
+void launch_outage_y(const DevPlan& P, const DevState& S, int B, const int32_t* outages, int k, const int4* bpos,
+                     const double* bval, int nbr, cudaStream_t st, Recorder* rec = nullptr);
+
 // Reset the loop control (prev = 1, cur = 0, it = 0) with the tolerance and
 // iteration limit of this solve.
 void launch_ctl_init(const DevState& S, int maxit, double tol, cudaStream_t st, Recorder* rec = nullptr);

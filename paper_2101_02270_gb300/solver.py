@@ -202,6 +202,36 @@ class Plan:
               "pf_branch_flows")
         return sf, st
 
+    def solve_outages(self, outages: torch.Tensor, sbus: torch.Tensor, v0: torch.Tensor, tol: float = 1e-8,
+                      maxit: int = 10, out=None):
+        """Newton-Raphson for branch-outage cases (pf_solve_batch_outages):
+        outages int32 [B, k] on the GPU (branch indices, -1 = none); each
+        instance's admittances are the base ones minus its outaged branches,
+        built on the device.  The plan must come from from_branches."""
+        B = sbus.shape[0]
+        self._check_bn(sbus, B)
+        self._check_bn(v0, B)
+        if outages.dtype != torch.int32 or outages.dim() != 2 or outages.shape[0] != B:
+            raise ValueError(f"outages must be int32 [{B}, k]")
+        if not getattr(self, "_branches_set", False):
+            f, t, r, x, b = (np.ascontiguousarray(a, dt) for a, dt in zip(
+                self._branches, (np.int32, np.int32, np.float64, np.float64, np.float64)))
+            check(lib.pf_plan_set_branches(self._h, f.shape[0], _lib._np_ptr(f), _lib._np_ptr(t), _lib._np_ptr(r),
+                                           _lib._np_ptr(x), _lib._np_ptr(b)), "pf_plan_set_branches")
+            self._branches_set = True
+        dev = sbus.device
+        if out is None:
+            v = torch.empty((B, self.n), dtype=torch.complex128, device=dev)
+            iters = torch.empty(B, dtype=torch.int32, device=dev)
+            status = torch.empty(B, dtype=torch.uint8, device=dev)
+        else:
+            v, iters, status = out
+        outages = outages.contiguous()
+        check(lib.pf_solve_batch_outages(self._h, B, _dptr(outages), outages.shape[1], _dptr(sbus), _dptr(v0),
+                                         float(tol), int(maxit), _dptr(v), _dptr(iters), _dptr(status), _stream()),
+              "pf_solve_batch_outages")
+        return v, iters, status
+
     def solve_y(self, ybus: torch.Tensor, sbus: torch.Tensor, v0: torch.Tensor, tol: float = 1e-8,
                 maxit: int = 10, out=None):
         """Newton-Raphson with per-instance admittances on this plan's pattern

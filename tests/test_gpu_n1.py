@@ -114,3 +114,40 @@ def test_branch_flows_against_oracle():
         np.add.at(acc, g.t, stt[k])
         assert np.max(np.abs(acc[pq] - S[k][pq])) < 1e-8
         assert np.max(np.abs(acc.real[pv] - S[k].real[pv])) < 1e-8
+
+
+@pytest.mark.parametrize("lu", ["fp64", "fp32"])
+def test_device_built_outage_cases(lu):
+    """Outage cases whose admittances are built on the device (base values
+    minus the outaged branches' stamps) give the results of the host-built
+    per-instance admittances; N-2 cases with a repeated index and an empty
+    slot match the oracle on their grids."""
+    g = gridgen.make_grid("mesh30_b64")
+    outage, level, ins, S = gridgen.n1_batch(g)
+    V0 = np.broadcast_to(g.v_set.astype(np.complex128), S.shape).copy()
+    with _plan(g, lu_precision=lu) as p:
+        Y = p.ybus_values(ins)
+        a = [t.cpu().numpy() for t in p.solve_y(_dev(Y), _dev(S), _dev(V0), TOL, 10)]
+        o = torch.from_numpy(outage.astype(np.int32)[:, None]).cuda()
+        b = [t.cpu().numpy() for t in p.solve_outages(o, _dev(S), _dev(V0), TOL, 10)]
+        assert np.array_equal(a[2], b[2])
+        assert np.max(np.abs(a[0] - b[0])) < 1e-10
+        if lu == "fp64":
+            assert np.array_equal(a[1], b[1])
+        # N-2: pairs of outages (plus a repeated index and an empty slot)
+        rng = np.random.default_rng(4)
+        B = 24
+        pairs = np.stack([rng.choice(len(outage) // 5, 2, replace=False) for _ in range(B)]).astype(np.int32)
+        pairs = outage[:len(outage) // 5][pairs].astype(np.int32)
+        extra = np.full((B, 2), -1, np.int32)
+        extra[0, 0] = pairs[0, 0]  # repeated: removed once
+        o2 = np.concatenate([pairs, extra], axis=1)
+        S2, V2 = S[:B], V0[:B]
+        v, it, st = (t.cpu().numpy() for t in p.solve_outages(torch.from_numpy(o2).cuda(), _dev(S2), _dev(V2), TOL, 10))
+    for bi in range(0, B, 3):
+        keep = np.ones(g.n_branch, bool)
+        keep[o2[bi][o2[bi] >= 0]] = False
+        Vo, ito, sto, Yo = _oracle_case(g, keep, S2[bi], V2[bi])
+        assert st[bi] == sto
+        if sto == 0:
+            assert np.max(np.abs(v[bi] - Vo)) < 1e-6
