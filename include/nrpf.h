@@ -69,6 +69,13 @@ typedef struct pf_options {
   int host_only;       /* 1: symbolic analysis only, no device memory; the plan
                           answers pf_plan_get_info / pf_plan_get_pattern and every
                           solve or stage call on it returns NRPF_ERR_ARG          */
+  int order_tries;     /* AMD only: minimum degree leaves ties between vertices of
+                          equal degree open; the plan tries this many seeded
+                          tie-breaks (seed 0: lowest bus index first) and keeps
+                          the one of least estimated refactor time (dense-block
+                          multiply-adds plus a precision-dependent weight times
+                          the sparse ones); 0 = default (128 up to 4,000 buses,
+                          512,000 / n above, at least 8), 1 = seed 0 only        */
 } pf_options;
 
 typedef struct pf_plan pf_plan;   /* opaque; owns its device arrays and workspace */
@@ -90,6 +97,7 @@ typedef struct pf_plan_info {
   int capacity;        /* batch capacity currently allocated                     */
   int lu_precision;
   int panel;           /* dense-block panel width in use                          */
+  int order_seed;      /* tie-break seed of the ordering kept (0 for NATURAL)     */
 } pf_plan_info;
 
 /* Fill pf_options with the defaults (AMD ordering, FP64 LU, dense_frac and

@@ -25,6 +25,13 @@ using nrpf::kTile;
 
 namespace {
 
+// seeded minimum-degree tie-breaks tried per plan when pf_options.order_tries
+// is 0: 128 up to 4,000 buses, fewer above so that the orderings take about
+// as long as the rest of the symbolic analysis, never fewer than 8
+int default_order_tries(int n) { return std::max(8, std::min(128, 512000 / std::max(n, 1))); }
+constexpr double kSparseWeightFp64 = 1.5;
+constexpr double kSparseWeightFp32 = 4.0;
+
 #define CK(call)                                   \
   do {                                             \
     cudaError_t e_ = (call);                       \
@@ -304,6 +311,7 @@ int pf_options_default(pf_options* opt) {
   opt->panel = 0;  /* chosen by precision at plan creation */
   opt->max_batch = 0;
   opt->host_only = 0;
+  opt->order_tries = 0;  /* default at plan creation */
   return NRPF_OK;
 }
 
@@ -364,16 +372,21 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
   // in FP32 (the dense block runs at FP32 rate, the sparse phase does not),
   // so the FP32 path hands more of the matrix to the dense block
   if (o.dense_frac == 0.0) o.dense_frac = o.lu_precision == NRPF_LU_FP32 ? 0.3 : 0.7;
+  if (o.order_tries == 0) o.order_tries = default_order_tries(n);
   if (o.lu_precision != NRPF_LU_FP64 && o.lu_precision != NRPF_LU_FP32) return NRPF_ERR_ARG;
   if (o.ordering != NRPF_ORDER_AMD && o.ordering != NRPF_ORDER_NATURAL) return NRPF_ERR_ARG;
-  if (!(o.dense_frac > 0.0) || o.max_batch < 0) return NRPF_ERR_ARG;
+  if (!(o.dense_frac > 0.0) || o.max_batch < 0 || o.order_tries < 0) return NRPF_ERR_ARG;
+  // relative time of a multiply-add of the sparse phase (level schedule and
+  // Schur tasks) to one of the dense block, from the kernels' measured times
+  // per multiply-add on the 2,000-bus meshed grid
+  const double sparse_weight = o.lu_precision == NRPF_LU_FP32 ? kSparseWeightFp32 : kSparseWeightFp64;
   pf_plan* p = new (std::nothrow) pf_plan();
   if (!p) return NRPF_ERR_NOMEM;
   std::string err;
   int rc;
   try {
     rc = nrpf::build_plan(n, rowptr, colidx, y_re, y_im, bus_type, o.ordering, o.dense_frac, o.panel,
-                          p->hp, err);
+                          o.order_tries, sparse_weight, p->hp, err);
   } catch (const std::bad_alloc&) {
     rc = NRPF_ERR_NOMEM;
   } catch (...) {
@@ -462,6 +475,7 @@ int pf_plan_get_info(const pf_plan* p, pf_plan_info* info) {
   info->capacity = p->capacity;
   info->lu_precision = p->lu_precision;
   info->panel = h.kb;
+  info->order_seed = (int)h.order_seed;
   return NRPF_OK;
 }
 

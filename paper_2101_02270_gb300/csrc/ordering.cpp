@@ -12,8 +12,31 @@ namespace nrpf {
 
 namespace {
 
+// splitmix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): the tie-break ranks of a seeded ordering.
+uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// rank[v] breaks ties between vertices of equal approximate degree: seed 0
+// keeps the vertex order, any other seed a Fisher-Yates shuffle of it.
+std::vector<int> tie_ranks(int nv, uint64_t seed) {
+  std::vector<int> rank(nv);
+  std::iota(rank.begin(), rank.end(), 0);
+  if (seed == 0) return rank;
+  uint64_t x = seed;
+  for (int i = nv - 1; i > 0; --i) {
+    const int j = (int)(splitmix64(x) % (uint64_t)(i + 1));
+    std::swap(rank[i], rank[j]);
+  }
+  return rank;
+}
+
 Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::vector<int>& w,
-                   double dense_frac, bool use_degree) {
+                   double dense_frac, bool use_degree, uint64_t seed) {
   std::vector<std::vector<int>> A(adj);   // variable -> adjacent live variables
   std::vector<std::vector<int>> E(nv);    // variable -> adjacent live elements
   std::vector<std::vector<int>> Le(nv);   // element -> boundary variables
@@ -25,13 +48,17 @@ Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::
   std::vector<std::vector<int>> lst(nv);  // per vertex: L column structure (vertices)
   long remaining_w = 0;
   for (int i = 0; i < nv; ++i) remaining_w += w[i];
+  // (degree, tie-break rank); byrank maps a rank back to its vertex
   std::set<std::pair<long, int>> heap;
+  const std::vector<int> rank = tie_ranks(nv, seed);
+  std::vector<int> byrank(nv);
+  for (int i = 0; i < nv; ++i) byrank[rank[i]] = i;
   if (use_degree) {
     for (int i = 0; i < nv; ++i) {
       long d = 0;
       for (int j : A[i]) d += w[j];
       deg[i] = d;
-      heap.insert({d, i});
+      heap.insert({d, rank[i]});
     }
   }
   Ordering out;
@@ -41,7 +68,7 @@ Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::
   for (; k < nv; ++k) {
     int p;
     if (use_degree) {
-      p = heap.begin()->second;
+      p = byrank[heap.begin()->second];
       if (dense_frac < 1.0 && nv - k > 1 &&
           (double)deg[p] >= dense_frac * (double)(remaining_w - w[p])) {
         break;  // remaining graph is dense: stop here
@@ -96,9 +123,9 @@ Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::
         if (e != p) ext += std::max(we[e], 0L);
       long d = std::min({remaining_w - w[i], deg[i] + lpw - w[i], ext});
       if (d != deg[i]) {
-        heap.erase({deg[i], i});
+        heap.erase({deg[i], rank[i]});
         deg[i] = d;
-        heap.insert({d, i});
+        heap.insert({d, rank[i]});
       }
     }
   }
@@ -106,7 +133,7 @@ Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::
   if (k < nv) {
     // Dense tail: remaining variables in ascending degree order.
     std::vector<int> rest;
-    for (auto& pr : heap) rest.push_back(pr.second);
+    for (auto& pr : heap) rest.push_back(byrank[pr.second]);
     for (int v : rest) out.order.push_back(v);
   }
   std::vector<int> pos(nv);
@@ -127,14 +154,40 @@ Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::
 }  // namespace
 
 Ordering amd_order(int nv, const std::vector<std::vector<int>>& adj, const std::vector<int>& w,
-                   double dense_frac) {
-  return eliminate(nv, adj, w, dense_frac, true);
+                   double dense_frac, uint64_t seed) {
+  return eliminate(nv, adj, w, dense_frac, true, seed);
 }
 
 Ordering natural_order(int nv, const std::vector<std::vector<int>>& adj, const std::vector<int>& w) {
-  Ordering o = eliminate(nv, adj, w, 1.0, false);
+  Ordering o = eliminate(nv, adj, w, 1.0, false, 0);
   o.dense_start = nv;
   return o;
+}
+
+OrderingCost ordering_cost(const Ordering& o, const std::vector<int>& w, int panel) {
+  OrderingCost c;
+  const int nv = (int)o.order.size();
+  // scalar L column of the t-th unknown of the vertex at position q: the
+  // vertex's later unknowns plus every unknown of the vertices in lstruct[q];
+  // a left-looking refactor spends r (scaling) + r^2 (updates) multiply-adds
+  // on a column with r entries below the diagonal (symmetric pattern)
+  int nd = 0;
+  for (int q = 0; q < nv; ++q) {
+    const int wq = w[o.order[q]];
+    if (q >= o.dense_start) { nd += wq; continue; }
+    double ext = 0;
+    for (int r : o.lstruct[q]) ext += w[o.order[r]];
+    for (int t = 0; t < wq; ++t) {
+      const double r = (double)(wq - 1 - t) + ext;
+      c.sparse_fma += r + r * r;
+    }
+  }
+  const int ndp = nd ? (nd + panel - 1) / panel * panel : 0;
+  for (int k = 0; k < ndp; ++k) {
+    const double r = ndp - k - 1;
+    c.dense_fma += r + r * r;
+  }
+  return c;
 }
 
 }  // namespace nrpf

@@ -21,9 +21,21 @@ struct Ordering {
 // element absorption and weighted (scalar) external degrees.  Elimination stops
 // once the cheapest remaining vertex is adjacent to at least `dense_frac` of the
 // remaining scalar unknowns; the rest is ordered by ascending degree and marked
-// dense.  adj must be symmetric without self loops.
+// dense.  adj must be symmetric without self loops.  Ties between vertices of
+// equal approximate degree go to the lower vertex index when seed is 0, else to
+// the lower rank in a seeded random permutation of the vertices (minimum degree
+// leaves the tie-break open; on meshed grids it moves the fill by about 10%).
 Ordering amd_order(int nv, const std::vector<std::vector<int>>& adj, const std::vector<int>& w,
-                   double dense_frac);
+                   double dense_frac, uint64_t seed = 0);
+
+// Multiply-adds of one LU refactorisation under an ordering (one instance),
+// split into the columns eliminated sparsely (including their updates of the
+// dense block) and the dense block itself padded to `panel`.
+struct OrderingCost {
+  double sparse_fma = 0;
+  double dense_fma = 0;
+};
+OrderingCost ordering_cost(const Ordering& o, const std::vector<int>& w, int panel);
 
 // Natural order (identity), same symbolic output: used by tests.
 Ordering natural_order(int nv, const std::vector<std::vector<int>>& adj, const std::vector<int>& w);

@@ -64,11 +64,15 @@ int validate(int n, const int32_t* rowptr, const int32_t* colidx, const double* 
 
 int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double* yre,
                const double* yim, const int8_t* bt, int ordering, double dense_frac, int kb,
-               HostPlan& P, std::string& err) {
+               int order_tries, double sparse_weight, HostPlan& P, std::string& err) {
   int rc = validate(n, rowptr, colidx, yre, yim, bt, err);
   if (rc) return rc;
   if (kb != 4 && kb != 8 && kb != 16 && kb != 32 && kb != 64) {
     err = "panel must be 4, 8, 16, 32 or 64";
+    return NRPF_ERR_ARG;
+  }
+  if (order_tries < 1 || !(sparse_weight >= 0.0)) {
+    err = "order_tries must be >= 1 and sparse_weight >= 0";
     return NRPF_ERR_ARG;
   }
   const int nnzY = rowptr[n];
@@ -100,8 +104,22 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
       if (c != i && vid[c] >= 0) adj[v].push_back(vid[c]);
     }
   }
-  Ordering ord = ordering == NRPF_ORDER_NATURAL ? natural_order(nv, adj, w)
-                                                : amd_order(nv, adj, w, dense_frac);
+  Ordering ord;
+  if (ordering == NRPF_ORDER_NATURAL) {
+    ord = natural_order(nv, adj, w);
+  } else {
+    double best = 0;
+    for (int t = 0; t < order_tries; ++t) {
+      Ordering o = amd_order(nv, adj, w, dense_frac, (uint64_t)t);
+      const OrderingCost c = ordering_cost(o, w, kb);
+      const double cost = c.dense_fma + sparse_weight * c.sparse_fma;
+      if (t == 0 || cost < best) {
+        best = cost;
+        ord = std::move(o);
+        P.order_seed = (uint64_t)t;
+      }
+    }
+  }
 
   // ---- scalar positions: per bus in elimination order, angle then |V| ----
   P.th_pos.assign(n, -1);

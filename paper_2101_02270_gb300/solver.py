@@ -40,7 +40,8 @@ class Plan:
     """Symbolic plan for one Ybus sparsity pattern (pf_plan_create)."""
 
     def __init__(self, n, rowptr, colidx, y_re, y_im, bus_type, lu_precision="fp64",
-                 ordering="amd", dense_frac=0.0, panel=0, max_batch=0, host_only=False):
+                 ordering="amd", dense_frac=0.0, panel=0, max_batch=0, host_only=False,
+                 order_tries=0):
         self.n = int(n)
         self._rowptr = np.ascontiguousarray(rowptr, np.int32)
         self._colidx = np.ascontiguousarray(colidx, np.int32)
@@ -55,6 +56,7 @@ class Plan:
         opt.panel = int(panel)
         opt.max_batch = int(max_batch)
         opt.host_only = int(bool(host_only))
+        opt.order_tries = int(order_tries)
         h = C.c_void_p()
         check(lib.pf_plan_create(self.n, _lib._np_ptr(self._rowptr), _lib._np_ptr(self._colidx),
                                  _lib._np_ptr(self._yre), _lib._np_ptr(self._yim), _lib._np_ptr(self._bt),

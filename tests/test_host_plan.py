@@ -186,3 +186,45 @@ def test_dense_update_accounting_matches_lu_arithmetic():
         u12 = sum((n - k - inner) * sum(range(inner)) for k in range(0, n, inner))
         assert upd + panel + u12 == total, kb
     assert bench.dense_update_flop(n, 32) == bench.dense_update_flop(n, 16) == bench.dense_update_flop(n, 64)
+
+
+def _weighted_refactor_cost(info, sparse_weight):
+    ndp = info["dense_pad"]
+    dense = sum((ndp - k - 1) + (ndp - k - 1) ** 2 for k in range(ndp))
+    return dense + sparse_weight * (info["lu_fma"] - dense)
+
+
+@pytest.mark.parametrize("prec,weight", [("fp64", 1.5), ("fp32", 4.0)])
+def test_seeded_orderings_never_raise_the_estimated_refactor_cost(prec, weight):
+    """Minimum degree leaves ties open; the plan tries order_tries seeded
+    tie-breaks and keeps the cheapest.  The cost it ranks by must be the
+    plan's own multiply-add count (dense block + weight x sparse phase), so the
+    kept cost falls monotonically with the number of tries, and seed 0 (lowest
+    bus index first) is what one try gives."""
+    g = gridgen.make_grid("mesh2000_b10k")
+    prev = None
+    for tries in (1, 2, 4, 16, 64):
+        i = _plan(g, lu_precision=prec, order_tries=tries).info
+        assert 0 <= i["order_seed"] < tries
+        c = _weighted_refactor_cost(i, weight)
+        if prev is not None:
+            assert c <= prev * (1 + 1e-12)
+        else:
+            assert i["order_seed"] == 0
+            first = c
+        prev = c
+    if prec == "fp64":
+        # on this meshed grid the tie-break moves the FP64 cost by > 5 %
+        assert prev < 0.95 * first
+    # the default is deterministic: same seed and counts twice
+    a, b = _plan(g, lu_precision=prec).info, _plan(g, lu_precision=prec).info
+    assert a["order_seed"] == b["order_seed"] and a["lu_fma"] == b["lu_fma"]
+    # natural ordering ignores the option
+    assert _plan(gridgen.make_grid("mesh30_b64"), ordering="natural", order_tries=5).info["order_seed"] == 0
+
+
+def test_order_tries_rejects_negative():
+    pf = _lib()
+    g = gridgen.make_grid("mesh30_b64")
+    with pytest.raises(pf.NrpfError, match="invalid argument"):
+        _plan(g, order_tries=-1)
