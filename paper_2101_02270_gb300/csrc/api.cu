@@ -30,7 +30,7 @@ namespace {
 // as long as the rest of the symbolic analysis, never fewer than 8
 int default_order_tries(int n) { return std::max(8, std::min(128, 512000 / std::max(n, 1))); }
 constexpr double kSparseWeightFp64 = 1.5;
-constexpr double kSparseWeightFp32 = 4.0;
+constexpr double kSparseWeightFp32 = 15.0;
 
 #define CK(call)                                   \
   do {                                             \

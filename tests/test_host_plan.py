@@ -194,7 +194,7 @@ def _weighted_refactor_cost(info, sparse_weight):
     return dense + sparse_weight * (info["lu_fma"] - dense)
 
 
-@pytest.mark.parametrize("prec,weight", [("fp64", 1.5), ("fp32", 4.0)])
+@pytest.mark.parametrize("prec,weight", [("fp64", 1.5), ("fp32", 15.0)])
 def test_seeded_orderings_never_raise_the_estimated_refactor_cost(prec, weight):
     """Minimum degree leaves ties open; the plan tries order_tries seeded
     tie-breaks and keeps the cheapest.  The cost it ranks by must be the
