@@ -432,15 +432,22 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
 
 // Schur complement of the sparse columns into the dense block, after the
 // sparse levels (every U(k, j) is then final).  A warp per (dense column j,
-// chunk of 32 dense rows) and tile: the products L(i, k) U(k, j) of all
-// sparse columns k are summed per row in shared memory (one column of 32
-// rows per lane), then subtracted from A(i, j) once.  The warp reads 32
-// entries with one coalesced load and hands them out by shuffles, so the
-// L and U loads of eight entries are in flight together.
+// chunk of 32 dense rows) and tile: the rows live in shared memory (one
+// column of 32 rows per lane) while the products L(i, k) U(k, j) of all
+// sparse columns k are applied, then go back once.  The warp reads 32 entries
+// with one coalesced load and hands them out by shuffles, so the L and U loads
+// of eight entries are in flight together.
+//   FP64 (bound by the FP64 pipe): each row starts from A(i, j) and takes the
+//   subtractions, in the order of the sparse columns as a left-looking
+//   column does; no separate subtraction pass.  At most 72 registers: 7 CTAs
+//   per SM, the shared-memory limit.
+//   FP32 (bound by load latency): each row starts from 0, sums the products
+//   and is subtracted from A(i, j) at the end, which keeps the register count
+//   and so the warps per SM up.
 constexpr int kSchurWarps = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kSchurWarps) k_schur(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
+__global__ void __launch_bounds__(32 * kSchurWarps, sizeof(T) == 8 ? 7 : 1) k_schur(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;
   __shared__ T acc[kSchurWarps][32][32];
   const int lane = threadIdx.x, w = threadIdx.y;
@@ -451,9 +458,21 @@ __global__ void __launch_bounds__(32 * kSchurWarps) k_schur(DevPlan P, DevState 
   T* __restrict__ LUb = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;
   const T* __restrict__ LU = LUb + lane;  // sparse positions (< NS): p * 32
   T(*a)[32] = acc[w];
-#pragma unroll
-  for (int r = 0; r < 32; ++r) a[r][lane] = (T)0;
   const int4 task = P.schur_task[t];
+  // A(i, j) = J(i, j) where J has an entry, else 0: the block is not zeroed
+  // before the refactorisation; the Jacobian fill has written its entries
+  const uint32_t jm = P.schur_jmask[t];
+  constexpr bool kSeeded = DenseGroup<T>::G != 4;
+  if constexpr (kSeeded) {
+    const int64_t col = P.NS + (int64_t)task.x * P.ndp + 32 * task.y;
+    const int nr = min(32, P.ndp - 32 * task.y);
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r)
+      a[r][lane] = (r < nr && (jm >> r & 1u)) ? LUb[lu_off<T>(col + r, P.NS, lane)] : (T)0;
+  } else {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) a[r][lane] = (T)0;
+  }
   for (int eb = task.z; eb < task.w; eb += 32) {
     const int cnt = min(32, task.w - eb);
     const int32_t xl = lane < cnt ? P.schur_ent[eb + lane] : 0;
@@ -470,20 +489,19 @@ __global__ void __launch_bounds__(32 * kSchurWarps) k_schur(DevPlan P, DevState 
         l[z] = ok ? LU[(size_t)(x >> 5) * kTile] : (T)0;
         u[z] = ok ? LU[(size_t)up * kTile] : (T)0;
       }
-      // entries of one task keep their order: sums per row accumulate in
-      // the order of the sparse columns
+      // entries of one task keep their order (the sparse columns ascending)
 #pragma unroll
       for (int z = 0; z < 8; ++z)
-        if (i + z < cnt) a[r[z]][lane] += l[z] * u[z];
+        if (i + z < cnt) {
+          if constexpr (kSeeded) a[r[z]][lane] -= l[z] * u[z];
+          else a[r[z]][lane] += l[z] * u[z];
+        }
     }
   }
-  // every row of the chunk below the padded size: A(i, j) = J(i, j) or 0,
-  // minus the sum (the block is not zeroed before the refactorisation; the
-  // Jacobian fill has written its entries)
-  const uint32_t jm = P.schur_jmask[t];
-  if constexpr (DenseGroup<T>::G == 4) {
+  // every row of the chunk below the padded size is written back
+  if constexpr (!kSeeded) {
     // grouped FP32 block: rows 4g .. 4g+3 of the chunk are one 16-byte word
-    // per lane
+    // per lane; A(i, j) minus the sum
     float4* __restrict__ A4 = reinterpret_cast<float4*>(LUb + (size_t)P.NS * kTile);
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
@@ -502,10 +520,7 @@ __global__ void __launch_bounds__(32 * kSchurWarps) k_schur(DevPlan P, DevState 
     const int64_t col = P.NS + (int64_t)task.x * P.ndp + 32 * task.y;
     const int nr = min(32, P.ndp - 32 * task.y);
 #pragma unroll 4
-    for (int r = 0; r < nr; ++r) {
-      T* q = LUb + lu_off<T>(col + r, P.NS, lane);
-      *q = (jm >> r & 1u) ? *q - a[r][lane] : -a[r][lane];
-    }
+    for (int r = 0; r < nr; ++r) LUb[lu_off<T>(col + r, P.NS, lane)] = a[r][lane];
   }
 }
 
