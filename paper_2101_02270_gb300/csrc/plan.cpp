@@ -5,9 +5,11 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <numeric>
 #include <set>
+#include <thread>
 
 #include "../../include/nrpf.h"
 #include "ordering.h"
@@ -108,17 +110,37 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
   if (ordering == NRPF_ORDER_NATURAL) {
     ord = natural_order(nv, adj, w);
   } else {
-    double best = 0;
-    for (int t = 0; t < order_tries; ++t) {
-      Ordering o = amd_order(nv, adj, w, dense_frac, (uint64_t)t);
-      const OrderingCost c = ordering_cost(o, w, kb);
-      const double cost = c.dense_fma + sparse_weight * c.sparse_fma;
-      if (t == 0 || cost < best) {
-        best = cost;
-        ord = std::move(o);
-        P.order_seed = (uint64_t)t;
+    // the tries are independent: they run on the host's threads, and the
+    // ordering kept is the cheapest, the lowest seed among equal costs, for
+    // any thread count
+    std::vector<double> cost(order_tries, 0.0);
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::min(order_tries, (int)std::min(16u, hw));
+    std::atomic<int> next{0};
+    std::atomic<bool> failed{false};
+    auto work = [&] {
+      try {
+        for (int t; (t = next.fetch_add(1)) < order_tries;) {
+          const OrderingCost c = ordering_cost(amd_order(nv, adj, w, dense_frac, (uint64_t)t), w, kb);
+          cost[t] = c.dense_fma + sparse_weight * c.sparse_fma;
+        }
+      } catch (...) {
+        failed = true;
       }
+    };
+    if (nt <= 1) {
+      work();
+    } else {
+      std::vector<std::thread> pool;
+      for (int i = 0; i < nt; ++i) pool.emplace_back(work);
+      for (auto& th : pool) th.join();
     }
+    if (failed) { err = "out of host memory while ordering"; return NRPF_ERR_NOMEM; }
+    int best = 0;
+    for (int t = 1; t < order_tries; ++t)
+      if (cost[t] < cost[best]) best = t;
+    ord = amd_order(nv, adj, w, dense_frac, (uint64_t)best);
+    P.order_seed = (uint64_t)best;
   }
 
   // ---- scalar positions: per bus in elimination order, angle then |V| ----
