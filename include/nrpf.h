@@ -70,12 +70,15 @@ typedef struct pf_options {
                           answers pf_plan_get_info / pf_plan_get_pattern and every
                           solve or stage call on it returns NRPF_ERR_ARG          */
   int order_tries;     /* AMD only: minimum degree leaves ties between vertices of
-                          equal degree open; the plan tries this many seeded
-                          tie-breaks (seed 0: lowest bus index first) and keeps
-                          the one of least estimated refactor time (dense-block
+                          equal degree open.  With order_tries = T > 1 the plan
+                          tries T seeded tie-breaks (seed 0: lowest bus index
+                          first) of each of two elimination keys (minimum
+                          degree; mean local fill) and keeps the ordering of
+                          least estimated refactor time (dense-block
                           multiply-adds plus a precision-dependent weight times
-                          the sparse ones); 0 = default (128 up to 4,000 buses,
-                          512,000 / n above, at least 8), 1 = seed 0 only        */
+                          the sparse ones).  0 = default (T = 128 up to 4,000
+                          buses, 512,000 / n above, at least 8); 1 = minimum
+                          degree with seed 0 only                                */
 } pf_options;
 
 typedef struct pf_plan pf_plan;   /* opaque; owns its device arrays and workspace */
@@ -98,6 +101,7 @@ typedef struct pf_plan_info {
   int lu_precision;
   int panel;           /* dense-block panel width in use                          */
   int order_seed;      /* tie-break seed of the ordering kept (0 for NATURAL)     */
+  int order_key;       /* its elimination key: 0 minimum degree, 1 mean local fill */
 } pf_plan_info;
 
 /* Fill pf_options with the defaults (AMD ordering, FP64 LU, dense_frac and

@@ -36,7 +36,7 @@ class pf_plan_info(C.Structure):
                 ("dense_pad", C.c_int), ("lu_levels", C.c_int), ("fwd_levels", C.c_int),
                 ("bwd_levels", C.c_int), ("lu_fma", C.c_double), ("solve_fma", C.c_double),
                 ("capacity", C.c_int), ("lu_precision", C.c_int), ("panel", C.c_int),
-                ("order_seed", C.c_int)]
+                ("order_seed", C.c_int), ("order_key", C.c_int)]
 
 
 NKCLASSES = 16

@@ -476,6 +476,7 @@ int pf_plan_get_info(const pf_plan* p, pf_plan_info* info) {
   info->lu_precision = p->lu_precision;
   info->panel = h.kb;
   info->order_seed = (int)h.order_seed;
+  info->order_key = h.order_key;
   return NRPF_OK;
 }
 

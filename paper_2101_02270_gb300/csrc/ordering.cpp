@@ -36,19 +36,27 @@ std::vector<int> tie_ranks(int nv, uint64_t seed) {
 }
 
 Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::vector<int>& w,
-                   double dense_frac, bool use_degree, uint64_t seed) {
+                   double dense_frac, bool use_degree, uint64_t seed, OrderKey okey) {
   std::vector<std::vector<int>> A(adj);   // variable -> adjacent live variables
   std::vector<std::vector<int>> E(nv);    // variable -> adjacent live elements
   std::vector<std::vector<int>> Le(nv);   // element -> boundary variables
   std::vector<long> Lw(nv, 0);            // weighted size of Le
   std::vector<char> elim(nv, 0), absorbed(nv, 0);
-  std::vector<long> deg(nv, 0);
+  std::vector<long> deg(nv, 0), key(nv, 0);
+  // heap key of a variable of approximate external degree d whose newest
+  // element leaves c of those unknowns already connected to each other
+  auto score = [&](int i, long d, long c) -> long {
+    if (okey == OrderKey::kDegree) return d;
+    // mean local fill: the new pairs among the d neighbours, (d^2 - c^2)/2,
+    // over the unknowns of the vertex (its weight)
+    return (d * d - c * c) / w[i];
+  };
   std::vector<int> mark(nv, -1), we_mark(nv, -1);
   std::vector<long> we(nv, 0);
   std::vector<std::vector<int>> lst(nv);  // per vertex: L column structure (vertices)
   long remaining_w = 0;
   for (int i = 0; i < nv; ++i) remaining_w += w[i];
-  // (degree, tie-break rank); byrank maps a rank back to its vertex
+  // (key, tie-break rank); byrank maps a rank back to its vertex
   std::set<std::pair<long, int>> heap;
   const std::vector<int> rank = tie_ranks(nv, seed);
   std::vector<int> byrank(nv);
@@ -58,7 +66,8 @@ Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::
       long d = 0;
       for (int j : A[i]) d += w[j];
       deg[i] = d;
-      heap.insert({d, rank[i]});
+      key[i] = score(i, d, 0);
+      heap.insert({key[i], rank[i]});
     }
   }
   Ordering out;
@@ -122,16 +131,18 @@ Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::
       for (int e : E[i])
         if (e != p) ext += std::max(we[e], 0L);
       long d = std::min({remaining_w - w[i], deg[i] + lpw - w[i], ext});
-      if (d != deg[i]) {
-        heap.erase({deg[i], rank[i]});
-        deg[i] = d;
-        heap.insert({d, rank[i]});
+      const long kk = score(i, d, lpw - w[i]);
+      if (kk != key[i]) {
+        heap.erase({key[i], rank[i]});
+        key[i] = kk;
+        heap.insert({kk, rank[i]});
       }
+      deg[i] = d;
     }
   }
   out.dense_start = k;
   if (k < nv) {
-    // Dense tail: remaining variables in ascending degree order.
+    // Dense tail: remaining variables in ascending key order.
     std::vector<int> rest;
     for (auto& pr : heap) rest.push_back(byrank[pr.second]);
     for (int v : rest) out.order.push_back(v);
@@ -154,12 +165,12 @@ Ordering eliminate(int nv, const std::vector<std::vector<int>>& adj, const std::
 }  // namespace
 
 Ordering amd_order(int nv, const std::vector<std::vector<int>>& adj, const std::vector<int>& w,
-                   double dense_frac, uint64_t seed) {
-  return eliminate(nv, adj, w, dense_frac, true, seed);
+                   double dense_frac, uint64_t seed, OrderKey key) {
+  return eliminate(nv, adj, w, dense_frac, true, seed, key);
 }
 
 Ordering natural_order(int nv, const std::vector<std::vector<int>>& adj, const std::vector<int>& w) {
-  Ordering o = eliminate(nv, adj, w, 1.0, false, 0);
+  Ordering o = eliminate(nv, adj, w, 1.0, false, 0, OrderKey::kDegree);
   o.dense_start = nv;
   return o;
 }

@@ -21,12 +21,23 @@ struct Ordering {
 // element absorption and weighted (scalar) external degrees.  Elimination stops
 // once the cheapest remaining vertex is adjacent to at least `dense_frac` of the
 // remaining scalar unknowns; the rest is ordered by ascending degree and marked
-// dense.  adj must be symmetric without self loops.  Ties between vertices of
-// equal approximate degree go to the lower vertex index when seed is 0, else to
-// the lower rank in a seeded random permutation of the vertices (minimum degree
-// leaves the tie-break open; on meshed grids it moves the fill by about 10%).
+// dense.  adj must be symmetric without self loops.
+//
+// key picks the vertex eliminated next:
+//  - kDegree: least approximate external degree d (minimum degree);
+//  - kMeanFill: least mean local fill, (d^2 - c^2) / w[v], where c counts the
+//    unknowns among the d that the newest element adjacent to v already
+//    connects to each other.  This is the idea of the approximate minimum mean
+//    local fill heuristic (Ng & Raghavan, "Performance of greedy ordering
+//    heuristics for sparse Cholesky factorization", SIMAX 1999), in the
+//    simplified form that only the newest element is subtracted.
+// Ties between equal keys go to the lower vertex index when seed is 0, else to
+// the lower rank in a seeded random permutation of the vertices.  Minimum
+// degree leaves the tie-break open; on meshed grids it moves the fill by
+// about 10%.
+enum class OrderKey { kDegree = 0, kMeanFill = 1 };
 Ordering amd_order(int nv, const std::vector<std::vector<int>>& adj, const std::vector<int>& w,
-                   double dense_frac, uint64_t seed = 0);
+                   double dense_frac, uint64_t seed = 0, OrderKey key = OrderKey::kDegree);
 
 // Multiply-adds of one LU refactorisation under an ordering (one instance),
 // split into the columns eliminated sparsely (including their updates of the

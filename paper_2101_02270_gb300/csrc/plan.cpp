@@ -110,18 +110,22 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
   if (ordering == NRPF_ORDER_NATURAL) {
     ord = natural_order(nv, adj, w);
   } else {
-    // the tries are independent: they run on the host's threads, and the
-    // ordering kept is the cheapest, the lowest seed among equal costs, for
-    // any thread count
-    std::vector<double> cost(order_tries, 0.0);
+    // one try: minimum degree, seed 0; more: seeds 0 .. order_tries-1 with
+    // each key (try t: key t / order_tries, seed t % order_tries).  The tries
+    // are independent: they run on the host's threads, and the ordering kept
+    // is the cheapest, the lowest try among equal costs, for any thread count
+    const int ntries = order_tries > 1 ? 2 * order_tries : 1;
+    auto key_of = [&](int t) { return t < order_tries ? OrderKey::kDegree : OrderKey::kMeanFill; };
+    std::vector<double> cost(ntries, 0.0);
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int nt = std::min(order_tries, (int)std::min(16u, hw));
+    const int nt = std::min(ntries, (int)std::min(16u, hw));
     std::atomic<int> next{0};
     std::atomic<bool> failed{false};
     auto work = [&] {
       try {
-        for (int t; (t = next.fetch_add(1)) < order_tries;) {
-          const OrderingCost c = ordering_cost(amd_order(nv, adj, w, dense_frac, (uint64_t)t), w, kb);
+        for (int t; (t = next.fetch_add(1)) < ntries;) {
+          const Ordering o = amd_order(nv, adj, w, dense_frac, (uint64_t)(t % order_tries), key_of(t));
+          const OrderingCost c = ordering_cost(o, w, kb);
           cost[t] = c.dense_fma + sparse_weight * c.sparse_fma;
         }
       } catch (...) {
@@ -137,10 +141,11 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
     }
     if (failed) { err = "out of host memory while ordering"; return NRPF_ERR_NOMEM; }
     int best = 0;
-    for (int t = 1; t < order_tries; ++t)
+    for (int t = 1; t < ntries; ++t)
       if (cost[t] < cost[best]) best = t;
-    ord = amd_order(nv, adj, w, dense_frac, (uint64_t)best);
-    P.order_seed = (uint64_t)best;
+    ord = amd_order(nv, adj, w, dense_frac, (uint64_t)(best % order_tries), key_of(best));
+    P.order_seed = (uint64_t)(best % order_tries);
+    P.order_key = (int)key_of(best);
   }
 
   // ---- scalar positions: per bus in elimination order, angle then |V| ----

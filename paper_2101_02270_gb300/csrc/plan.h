@@ -63,14 +63,17 @@ struct HostPlan {
   int64_t nnz_j = 0, nnz_pattern = 0;
   double lu_fma = 0, solve_fma = 0;
   uint64_t order_seed = 0;                  // tie-break seed of the AMD ordering kept
+  int order_key = 0;                        // its key: 0 minimum degree, 1 mean local fill
 
   int64_t pos(int r, int c) const;  // A position of (r, c); -1 if not stored
 };
 
-// Build the plan.  With the AMD ordering, order_tries seeded tie-breaks
-// (seeds 0 .. order_tries-1) are tried and the one of least estimated refactor
-// time kept: dense-block multiply-adds plus sparse_weight times the sparse
-// ones.  Returns 0 or a negative NRPF_ERR_* code with a message.
+// Build the plan.  With the AMD ordering and order_tries > 1, seeds
+// 0 .. order_tries-1 of each elimination key (minimum degree, mean local fill)
+// are tried and the ordering of least estimated refactor time kept:
+// dense-block multiply-adds plus sparse_weight times the sparse ones.  One try
+// is minimum degree with seed 0.  Returns 0 or a negative NRPF_ERR_* code with
+// a message.
 int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double* yre,
                const double* yim, const int8_t* bus_type, int ordering, double dense_frac,
                int kb, int order_tries, double sparse_weight, HostPlan& out, std::string& err);

@@ -197,20 +197,21 @@ def _weighted_refactor_cost(info, sparse_weight):
 @pytest.mark.parametrize("prec,weight", [("fp64", 1.5), ("fp32", 15.0)])
 def test_seeded_orderings_never_raise_the_estimated_refactor_cost(prec, weight):
     """Minimum degree leaves ties open; the plan tries order_tries seeded
-    tie-breaks and keeps the cheapest.  The cost it ranks by must be the
-    plan's own multiply-add count (dense block + weight x sparse phase), so the
-    kept cost falls monotonically with the number of tries, and seed 0 (lowest
-    bus index first) is what one try gives."""
+    tie-breaks of each elimination key (minimum degree, mean local fill) and
+    keeps the cheapest.  The cost it ranks by must be the plan's own
+    multiply-add count (dense block + weight x sparse phase), so the kept cost
+    falls monotonically with the number of tries, and minimum degree with seed
+    0 (lowest bus index first) is what one try gives."""
     g = gridgen.make_grid("mesh2000_b10k")
     prev = None
     for tries in (1, 2, 4, 16, 64):
         i = _plan(g, lu_precision=prec, order_tries=tries).info
-        assert 0 <= i["order_seed"] < tries
+        assert 0 <= i["order_seed"] < tries and i["order_key"] in (0, 1)
         c = _weighted_refactor_cost(i, weight)
         if prev is not None:
             assert c <= prev * (1 + 1e-12)
         else:
-            assert i["order_seed"] == 0
+            assert i["order_seed"] == 0 and i["order_key"] == 0
             first = c
         prev = c
     if prec == "fp64":
@@ -218,7 +219,7 @@ def test_seeded_orderings_never_raise_the_estimated_refactor_cost(prec, weight):
         assert prev < 0.95 * first
     # the default is deterministic: same seed and counts twice
     a, b = _plan(g, lu_precision=prec).info, _plan(g, lu_precision=prec).info
-    assert a["order_seed"] == b["order_seed"] and a["lu_fma"] == b["lu_fma"]
+    assert (a["order_seed"], a["order_key"], a["lu_fma"]) == (b["order_seed"], b["order_key"], b["lu_fma"])
     # natural ordering ignores the option
     assert _plan(gridgen.make_grid("mesh30_b64"), ordering="natural", order_tries=5).info["order_seed"] == 0
 
