@@ -229,3 +229,16 @@ def test_order_tries_rejects_negative():
     g = gridgen.make_grid("mesh30_b64")
     with pytest.raises(pf.NrpfError, match="invalid argument"):
         _plan(g, order_tries=-1)
+
+
+def test_orderings_of_both_keys_give_closed_patterns():
+    """Plans of 300-bus meshed grids whose kept ordering comes from either
+    elimination key (minimum degree, mean local fill): the LU pattern is a
+    permutation of J's, holds J and is closed under elimination."""
+    keys = set()
+    for seed in range(4):
+        g = gridgen.make_grid("mesh2000_b10k", seed=seed, n=300, n_branch=390, n_pv=30)
+        info = _check_pattern(g, _plan(g))
+        keys.add(info["order_key"])
+        assert info["dense_dim"] > 0
+    assert keys == {0, 1}
