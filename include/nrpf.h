@@ -150,6 +150,10 @@ int pf_plan_get_pattern(const pf_plan* p, int32_t* pos_of_unknown, int64_t* colp
  *             held at their v0 values.
  * device out: v_out [B,n] complex (may alias v0), iters [B] Newton updates
  *             performed, status [B] per-instance outcome (NRPF_CONVERGED ...).
+ *             v_out of an NRPF_FAILED instance is unspecified: a bus whose
+ *             step was not finite keeps its previous value while the other
+ *             buses of the instance take theirs, so it mixes two iterates
+ *             (the second chance, pf_retry_failed, starts again from v0).
  * stream    : cudaStream_t of the caller (NULL = legacy default stream).
  * Asynchronous: returns after enqueueing.  Grows the workspace (device
  * allocation, synchronous) when B exceeds the plan's capacity.
@@ -409,6 +413,17 @@ int pf_warmstart_targets(int n, int B, const int32_t* nsidx, int nns, const doub
 int pf_warmstart_v0(int n, int B, const int32_t* nsidx, const int8_t* bus_type, int nns, const float* Y,
                     const double* v_flat, double* v0, void* stream);
 
+/* Screen of warm-started results (device in/out).  Newton from a guess can
+ * converge to another root of the power-flow equations than the one reached
+ * from flat start (a low-voltage solution).  The reading taken: the correct
+ * result is the flat-start solution, so a warm-started instance is redone
+ * from flat start when redo[b] = 1: status[b] != 0, a non-finite voltage, or
+ * min_i |v[b, i]| < vmin (p.u., >= 0).  v [B, n] complex128, status [B]
+ * (pf_solve_batch codes), redo [B] uint8.  No counterpart in the paper, which
+ * always starts from flat start (Sec. 3). */
+int pf_warmstart_screen(int n, int B, const double* v, const uint8_t* status, double vmin, uint8_t* redo,
+                        void* stream);
+
 /* ---- launch accounting and per-kernel device time ----
  * Kernel classes (index into the pf_profile arrays): 0 load (input transpose),
  * 1 store, 2 mismatch_jacobian, 3 check, 4 zero_lu, 5 set_ones,
@@ -456,10 +471,16 @@ int pf_fma_peak(double* fp64_tflops, double* fp32_tflops, void* stream);
  * device out: F [B,m] float64, row r = the equation at position r of
  *             A = P J P^T (pf_plan_get_pattern's pos_of_unknown maps J row u to
  *             position pos_of_unknown[u]); norm [B] = max |F| (a non-finite
- *             entry gives +inf).
+ *             entry gives +inf).  F and norm are float64 arithmetic and
+ *             float64 results for plans of either LU precision.  (The staged
+ *             pf_stage_mismatch of an FP32-LU plan reads F back from its FP32
+ *             right-hand side, so its F is rounded to float32; its norm is the
+ *             float64 one.)
  * The first call on a device looks up the array's device address (a runtime
  * query, once per device, with that device current); make that first call
- * before any stream capture begins.  Each call clears the part of the array it
+ * before any stream capture begins.  The address is kept for the life of the
+ * process: it does not survive cudaDeviceReset, after which this entry point
+ * must not be called again in the same process.  Each call clears the part of the array it
  * uses (stream-ordered memsets) and then runs one kernel.  All calls share the
  * array, so calls that overlap on the GPU (different streams, or threads)
  * race and give wrong norms: serialise them.  No cudaMalloc, cudaFree or

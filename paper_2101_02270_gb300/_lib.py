@@ -55,7 +55,7 @@ EXPORTS = ["pf_options_default", "pf_ybus_from_branches", "pf_plan_create", "pf_
            "pf_mlp_create", "pf_mlp_set_norm", "pf_mlp_fit_norm", "pf_mlp_params", "pf_mlp_grads",
            "pf_mlp_predict", "pf_mlp_train_step", "pf_mlp_error", "pf_mlp_destroy", "pf_gemm_bf16",
            "pf_gemm_set_variant",
-           "pf_warmstart_features", "pf_warmstart_targets", "pf_warmstart_v0",
+           "pf_warmstart_features", "pf_warmstart_targets", "pf_warmstart_v0", "pf_warmstart_screen",
            "pf_plan_destroy", "pf_status_str"]
 
 
@@ -111,6 +111,7 @@ def _load():
     lib.pf_warmstart_features.argtypes = [I, I, P, P, P]
     lib.pf_warmstart_targets.argtypes = [I, I, P, I, P, P, P]
     lib.pf_warmstart_v0.argtypes = [I, I, P, P, I, P, P, P, P]
+    lib.pf_warmstart_screen.argtypes = [I, I, P, P, C.c_double, P, P]
     lib.pf_plan_destroy.argtypes = [P]
     lib.pf_plan_destroy.restype = None
     lib.pf_status_str.argtypes = [I]

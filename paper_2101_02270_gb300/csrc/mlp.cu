@@ -579,6 +579,30 @@ __global__ void k_ws_v0(int n, int B, const int32_t* __restrict__ nsidx, const i
   sincos(ang, &sn, &cs);
   v0[i] = make_double2(mag * cs, mag * sn);
 }
+
+// Screen of warm-started results: one warp per instance takes min |V|^2 over
+// its buses; the instance is redone from flat start when it did not converge,
+// or when some magnitude is below vmin (a low-voltage root of the power-flow
+// equations, reached from a guess far from the operating point) or not finite.
+__global__ void k_ws_screen(int n, int B, const double2* __restrict__ v, const uint8_t* __restrict__ status,
+                            double vmin2, uint8_t* __restrict__ redo) {
+  const int b = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;
+  const double2* vb = v + (size_t)b * n;
+  double lo = INFINITY;
+  bool finite = true;
+  for (int k = lane; k < n; k += 32) {
+    const double2 x = vb[k];
+    const double m2 = x.x * x.x + x.y * x.y;
+    finite = finite && isfinite(m2);
+    lo = fmin(lo, m2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+  finite = __all_sync(0xffffffffu, finite);
+  if (lane == 0) redo[b] = (status[b] != 0 || !finite || lo < vmin2) ? 1 : 0;
+}
 }  // namespace
 
 extern "C" {
@@ -605,6 +629,15 @@ int pf_warmstart_v0(int n, int B, const int32_t* nsidx, const int8_t* bus_type, 
   if (B == 0) return NRPF_OK;
   k_ws_v0<<<nrpf::nb((int64_t)B * n), 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       n, B, nsidx, bus_type, Y, reinterpret_cast<const double2*>(v_flat), reinterpret_cast<double2*>(v0), nns);
+  return cudaGetLastError() == cudaSuccess ? NRPF_OK : NRPF_ERR_CUDA;
+}
+
+int pf_warmstart_screen(int n, int B, const double* v, const uint8_t* status, double vmin, uint8_t* redo,
+                        void* stream) {
+  if (n <= 0 || B < 0 || !(vmin >= 0.0) || (B > 0 && (!v || !status || !redo))) return NRPF_ERR_ARG;
+  if (B == 0) return NRPF_OK;
+  k_ws_screen<<<(B + 7) / 8, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      n, B, reinterpret_cast<const double2*>(v), status, vmin * vmin, redo);
   return cudaGetLastError() == cudaSuccess ? NRPF_OK : NRPF_ERR_CUDA;
 }
 

@@ -146,16 +146,31 @@ class WarmStart:
                                   _dptr(v_flat), _dptr(V0), _stream()), "v0")
         return V0
 
+    def screen(self, v, status, vmin=None):
+        """redo [B] (bool, device): instances whose warm-started result is not
+        taken: status != 0, a non-finite voltage, or a magnitude below vmin
+        p.u. (a low-voltage root of the power-flow equations)."""
+        vmin = self.vmin if vmin is None else vmin
+        redo = torch.empty(v.shape[0], dtype=torch.uint8, device=v.device)
+        check(lib.pf_warmstart_screen(self.n, v.shape[0], _dptr(v), _dptr(status), float(vmin), _dptr(redo),
+                                      _stream()), "pf_warmstart_screen")
+        return redo.bool()
+
+    # Magnitude floor of the screen.  Operating points of the workloads here
+    # stay above 0.8 p.u. (their load scale is chosen so); the low-voltage
+    # roots reached from bad guesses sit at a few hundredths of a p.u.
+    vmin = 0.5
+
     def solve(self, sbus, v_flat, tol=1e-8, maxit=10):
-        """NR from the network's guess; instances that do not converge from it
-        are re-solved from flat start.  Returns (v, iters, status, fallback)
-        with iters counting the updates of the run that produced v."""
+        """NR from the network's guess; instances whose result fails the
+        screen (no convergence, or a low-voltage root) are re-solved from flat
+        start, whose result is taken as it is.  Returns (v, iters, status,
+        fallback) with iters counting the updates of the run that produced v."""
         V0 = self.guess(sbus, v_flat)
         v, it, st = self.plan.solve(sbus, V0, tol, maxit)
-        bad = torch.nonzero(st != 0).flatten()
-        fb = torch.zeros_like(st, dtype=torch.bool)
+        fb = self.screen(v, st)
+        bad = torch.nonzero(fb).flatten()
         if bad.numel():
             v2, it2, st2 = self.plan.solve(sbus[bad].contiguous(), v_flat[bad].contiguous(), tol, maxit)
             v[bad], it[bad], st[bad] = v2, it2, st2
-            fb[bad] = True
         return v, it, st, fb

@@ -67,23 +67,30 @@ def test_mlp_forward_backward_vs_fp64_reference():
 
 
 def test_mlp_adamw_update():
+    """Six AdamW steps on the GPU against oracle.mlp.adamw_step, element by
+    element after every step.  The oracle keeps its own FP64 moments from
+    zero and takes the gradients the GPU computed at its own weights, so the
+    bias corrections of steps 2..6 and the changing learning rate are checked
+    as well as the first step."""
     ws = _ws()
     nin, nh1, nh2, nout, B = 64, 128, 128, 40, 50
     rng = np.random.default_rng(2)
     net = ws.MLP(nin, nh1, nh2, nout, bmax=64, seed=3)
-    P0 = net.params()
-    X = torch.from_numpy(rng.standard_normal((B, nin)).astype(np.float32)).cuda()
-    T = torch.from_numpy(rng.standard_normal((B, nout)).astype(np.float32)).cuda()
-    lr, wd = 1e-3, 0.01
-    net.train_step(X, T, lr=lr, wd=wd, update=True)
-    G = net.grads()
-    P1 = net.params()
-    for k, (p0, g, p1) in enumerate(zip(P0, G, P1)):
-        p = p0.astype(np.float64).copy()
-        m = np.zeros_like(p)
-        v = np.zeros_like(p)
-        omlp.adamw_step(p, g.astype(np.float64), m, v, 1, lr=lr, wd=wd if k % 2 == 0 else 0.0)
-        assert np.max(np.abs(p - p1)) < 1e-6, k
+    P = [p.astype(np.float64) for p in net.params()]
+    M = [np.zeros_like(p) for p in P]
+    V = [np.zeros_like(p) for p in P]
+    wd = 0.01
+    for step in range(1, 7):
+        X = torch.from_numpy(rng.standard_normal((B, nin)).astype(np.float32)).cuda()
+        T = torch.from_numpy(rng.standard_normal((B, nout)).astype(np.float32)).cuda()
+        lr = 1e-3 * (1.0 + 0.25 * step)
+        net.train_step(X, T, lr=lr, wd=wd, update=True)
+        G = net.grads()
+        P1 = net.params()
+        assert net.error() == 0
+        for k, (g, p1) in enumerate(zip(G, P1)):
+            omlp.adamw_step(P[k], g.astype(np.float64), M[k], V[k], step, lr=lr, wd=wd if k % 2 == 0 else 0.0)
+            assert np.max(np.abs(P[k] - p1)) < 1e-6 * step, (step, k, np.max(np.abs(P[k] - p1)))
 
 
 def test_warm_start_gain_on_2000_bus_grid():
@@ -163,3 +170,49 @@ def test_warm_start_falls_back_to_flat_start():
     assert int(fb.sum()) > 0
     # every fallback instance equals the flat-start result exactly
     assert torch.equal(v[fb], vf[fb]) and torch.equal(it[fb], itf[fb])
+
+
+def test_warm_start_low_voltage_root_is_redone_from_flat_start():
+    """Newton from a guess with one load bus at 0.1 p.u. converges on the
+    30-bus grid, but to a low-voltage root of the power-flow equations
+    (min |V| of a few hundredths).  The screen flags those instances and they
+    are re-solved from flat start: every result is then the flat-start
+    solution, which the oracle confirms."""
+    import paper_2101_02270_gb300 as pf
+    ws = _ws()
+    g = gridgen.make_grid("mesh30_b64")
+    plan = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type)
+    ns = np.flatnonzero(g.bus_type != 3)
+    nns = ns.size
+    low_bus = int(np.flatnonzero(g.bus_type == 1)[0])
+    net = ws.MLP(2 * g.n, 128, 128, 2 * nns, bmax=64, seed=0)
+    arrs = [np.zeros_like(a) for a in net.params()]
+    arrs[5][:nns] = 1.0                                  # flat magnitudes ...
+    arrs[5][int(np.flatnonzero(ns == low_bus)[0])] = 0.1  # ... but one load bus at 0.1 p.u.
+    net.set_params(arrs)
+    w = ws.WarmStart(plan, g.bus_type, net)
+    sc = gridgen.config_scenarios("mesh30_b64", g, batch=64)
+    S_np, V0_np = sc.sbus(g), sc.v0_flat(g)
+    S = torch.from_numpy(S_np).cuda()
+    Vf = torch.from_numpy(V0_np).cuda()
+    # the planted guess: Newton converges, to the wrong root, for some instances
+    vg, itg, stg = plan.solve(S, w.guess(S, Vf), 1e-8, 10)
+    low = (stg == 0) & (vg.abs().min(dim=1).values < 0.5)
+    assert int(low.sum()) > 0
+    v, it, st, fb = w.solve(S, Vf, 1e-8, 10)
+    assert bool(fb[low].all())
+    vf, itf, stf = plan.solve(S, Vf, 1e-8, 10)
+    assert torch.equal(v[fb], vf[fb]) and torch.equal(it[fb], itf[fb])
+    Vo, ito, sto = nrpf.newton_batch(oracle_ybus(g), S_np, V0_np, g.bus_type, 1e-8, 10)
+    assert np.array_equal(st.cpu().numpy(), sto)
+    assert np.max(np.abs(v.cpu().numpy() - Vo)) < 1e-6
+    # the screen itself: status, non-finite values and the floor
+    vt = torch.ones((3, 4), dtype=torch.complex128, device="cuda")
+    vt[1, 2] = 0.3
+    vt[2, 0] = float("nan")
+    stt = torch.tensor([0, 0, 0], dtype=torch.uint8, device="cuda")
+    w4 = ws.WarmStart.__new__(ws.WarmStart)
+    w4.n = 4
+    assert w4.screen(vt, stt, 0.5).tolist() == [False, True, True]
+    stt[0] = 1
+    assert w4.screen(vt, stt, 0.0).tolist() == [True, False, True]
