@@ -289,7 +289,9 @@ def test_loop_graph_matches_host_loops(lu, maxit):
 @pytest.mark.parametrize("lu,B,chunk", [("fp64", 100, 32), ("fp32", 100, 0), ("fp64", 64, 64), ("fp64", 45, 200)])
 def test_host_batch_chunks_match_device_solve(lu, B, chunk):
     """pf_solve_batch_host (chunks copied in and out around the solves,
-    ragged last chunk) gives exactly the device-resident solve's results."""
+    ragged last chunk) gives exactly the device-resident solve's results, and
+    those match the oracle (FP64 LU: same iterations; FP32 LU: at most three
+    more)."""
     g, S, V0 = case("mesh30_b64", batch=B)
     with _plan(g, lu_precision=lu) as p:
         v, it, st = p.solve(_dev(S), _dev(V0), TOL, 10)
@@ -303,12 +305,19 @@ def test_host_batch_chunks_match_device_solve(lu, B, chunk):
         torch.cuda.current_stream().synchronize()
     for a, b, c in ((v, vh, vp), (it, ith, itp), (st, sth, stp)):
         assert torch.equal(a.cpu(), b) and torch.equal(a.cpu(), c)
+    # and the host-batch results against the oracle, instance by instance
+    Vo, ito, sto = _oracle_solve(g, S, V0)
+    ith_np = ith.numpy()
+    _compare_newton(g, vh.numpy(), ith_np, sth.numpy(), Vo, ito, sto, S, check_iters=lu == "fp64")
+    if lu == "fp32":
+        ok = sto == 0
+        assert np.all(ith_np[ok] >= ito[ok]) and np.all(ith_np[ok] <= ito[ok] + 3)
 
 
 def test_host_batch_back_to_back_calls():
     """Consecutive host-batch calls without a synchronisation in between (the
     second call's copy-in overlaps the first call's solve) each return the
-    device solve of their own inputs."""
+    device solve of their own inputs, and the oracle's solution of them."""
     g, S1, V0 = case("mesh30_b64", batch=64)
     S2 = S1 * 0.9
     with _plan(g) as p:
@@ -321,3 +330,7 @@ def test_host_batch_back_to_back_calls():
     for r, o in zip(ref, outs):
         for a, b in zip(r, o):
             assert torch.equal(a, b)
+    # each call's results against the oracle on its own inputs
+    for S, o in zip((S1, S2, S1), outs):
+        Vo, ito, sto = _oracle_solve(g, S, V0)
+        _compare_newton(g, o[0].numpy(), o[1].numpy(), o[2].numpy(), Vo, ito, sto, S)
