@@ -135,8 +135,18 @@ int build_plan(int n, const int32_t* rowptr, const int32_t* colidx, const double
     if (nt <= 1) {
       work();
     } else {
+      // a thread that cannot be created leaves its share to the others and
+      // to this thread; the threads started are always joined
       std::vector<std::thread> pool;
-      for (int i = 0; i < nt; ++i) pool.emplace_back(work);
+      pool.reserve(nt);
+      for (int i = 0; i < nt; ++i) {
+        try {
+          pool.emplace_back(work);
+        } catch (...) {
+          break;
+        }
+      }
+      work();
       for (auto& th : pool) th.join();
     }
     if (failed) { err = "out of host memory while ordering"; return NRPF_ERR_NOMEM; }
