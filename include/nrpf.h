@@ -51,6 +51,15 @@ extern "C" {
                                     Newton step; mismatch/update stay float64) */
 #define NRPF_ORDER_AMD 0         /* approximate minimum degree on the bus graph */
 #define NRPF_ORDER_NATURAL 1     /* bus order as given (tests)                  */
+#define NRPF_DENSE_AUTO 0        /* instance-major for FP32 LU with a dense block
+                                    of at least NRPF_DENSE_IM_MIN unknowns and
+                                    panel 64, interleaved otherwise            */
+#define NRPF_DENSE_INTERLEAVED 1 /* dense block interleaved across the 32
+                                    instances of a tile (one lane each)        */
+#define NRPF_DENSE_INSTANCE_MAJOR 2 /* each instance's dense block its own
+                                    column-major matrix, factorised by CTA-tiled
+                                    kernels (FP32 LU only, panel 64)            */
+#define NRPF_DENSE_IM_MIN 512
 
 typedef struct pf_options {
   int lu_precision;    /* NRPF_LU_FP64 | NRPF_LU_FP32                              */
@@ -79,6 +88,9 @@ typedef struct pf_options {
                           the sparse ones).  0 = default (T = 128 up to 4,000
                           buses, 512,000 / n above, at least 8); 1 = minimum
                           degree with seed 0 only                                */
+  int dense_layout;    /* NRPF_DENSE_AUTO | NRPF_DENSE_INTERLEAVED |
+                          NRPF_DENSE_INSTANCE_MAJOR (storage and kernels of the
+                          dense block; results differ only by rounding)          */
 } pf_options;
 
 typedef struct pf_plan pf_plan;   /* opaque; owns its device arrays and workspace */
@@ -102,6 +114,7 @@ typedef struct pf_plan_info {
   int panel;           /* dense-block panel width in use                          */
   int order_seed;      /* tie-break seed of the ordering kept (0 for NATURAL)     */
   int order_key;       /* its elimination key: 0 minimum degree, 1 mean local fill */
+  int dense_layout;    /* NRPF_DENSE_INTERLEAVED or NRPF_DENSE_INSTANCE_MAJOR     */
 } pf_plan_info;
 
 /* Fill pf_options with the defaults (AMD ordering, FP64 LU, dense_frac and

@@ -26,7 +26,7 @@ class NrpfError(RuntimeError):
 class pf_options(C.Structure):
     _fields_ = [("lu_precision", C.c_int), ("ordering", C.c_int), ("dense_frac", C.c_double),
                 ("panel", C.c_int), ("max_batch", C.c_int), ("host_only", C.c_int),
-                ("order_tries", C.c_int)]
+                ("order_tries", C.c_int), ("dense_layout", C.c_int)]
 
 
 class pf_plan_info(C.Structure):
@@ -36,7 +36,7 @@ class pf_plan_info(C.Structure):
                 ("dense_pad", C.c_int), ("lu_levels", C.c_int), ("fwd_levels", C.c_int),
                 ("bwd_levels", C.c_int), ("lu_fma", C.c_double), ("solve_fma", C.c_double),
                 ("capacity", C.c_int), ("lu_precision", C.c_int), ("panel", C.c_int),
-                ("order_seed", C.c_int), ("order_key", C.c_int)]
+                ("order_seed", C.c_int), ("order_key", C.c_int), ("dense_layout", C.c_int)]
 
 
 NKCLASSES = 16

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnrpf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "kernels.cu", "mlp.cu", "multi.cu", "noalloc.cu", "peak.cu", "flows.cu", "plan.cpp",
+SOURCES = ["api.cu", "kernels.cu", "dense_im.cu", "mlp.cu", "multi.cu", "noalloc.cu", "peak.cu", "flows.cu", "plan.cpp",
            "ordering.cpp", "retry.cpp",
            "cpu_batch.cpp"]
 

@@ -116,7 +116,9 @@ int ensure_capacity(pf_plan* p, int B) {
   AL(nb, qsp, double*);
   AL((size_t)(h.s + h.ndp) * Bp * w, x, void*);
   AL((size_t)h.NLU * Bp * w, lu, void*);
-  AL((size_t)std::max(h.kb, 1) * Bp * w, inv, void*);
+  // inverse pivots of the current diagonal block (interleaved dense block),
+  // or U11^-1 and L11^-1 of the current 64 x 64 block (instance-major)
+  AL(p->dp.dim ? (size_t)2 * 64 * 64 * Bp * sizeof(float) : (size_t)std::max(h.kb, 1) * Bp * w, inv, void*);
   AL((size_t)Bp * sizeof(unsigned long long), norm, unsigned long long*);
   AL((size_t)Bp * 4, iters, int32_t*);
   AL((size_t)Bp * 4, status, int32_t*);
@@ -125,6 +127,14 @@ int ensure_capacity(pf_plan* p, int B) {
   AL(sizeof(nrpf::SolveCtl), ctl, nrpf::SolveCtl*);
 #undef AL
   CK(cudaMemset(s.ctl, 0, sizeof(nrpf::SolveCtl)));
+  if (p->dp.dim && h.ndp > 0) {
+    // TMA descriptors of this workspace's dense blocks
+    if (!nrpf::make_dense_im_maps(p->dp, s.lu, Bp, &p->im_maps)) {
+      free_ws(p);
+      return NRPF_ERR_CUDA;
+    }
+    s.im_maps = &p->im_maps;
+  }
   if (!p->h_prev) CK(cudaHostAlloc(reinterpret_cast<void**>(&p->h_prev), sizeof(int32_t), cudaHostAllocDefault));
   p->st = s;
   p->capacity = Bp;
@@ -312,6 +322,7 @@ int pf_options_default(pf_options* opt) {
   opt->max_batch = 0;
   opt->host_only = 0;
   opt->order_tries = 0;  /* default at plan creation */
+  opt->dense_layout = NRPF_DENSE_AUTO;
   return NRPF_OK;
 }
 
@@ -364,6 +375,12 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
   pf_options o;
   pf_options_default(&o);
   if (opt) o = *opt;
+  if (o.dense_layout < NRPF_DENSE_AUTO || o.dense_layout > NRPF_DENSE_INSTANCE_MAJOR) return NRPF_ERR_ARG;
+  // the instance-major kernels take FP32 blocks padded to a multiple of 64
+  if (o.dense_layout == NRPF_DENSE_INSTANCE_MAJOR &&
+      (o.lu_precision != NRPF_LU_FP32 || (o.panel != 0 && o.panel != 64)))
+    return NRPF_ERR_ARG;
+  const bool im_ok = o.lu_precision == NRPF_LU_FP32 && (o.panel == 0 || o.panel == 64);
   // default panel width by precision: FP32 needs the wider panel to feed its
   // FMA pipes with fewer passes over the trailing block
   if (o.panel == 0) o.panel = o.lu_precision == NRPF_LU_FP32 ? 64 : 8;
@@ -398,6 +415,10 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
   }
   p->lu_precision = o.lu_precision;
   p->host_only = o.host_only != 0;
+  // instance-major dense block: FP32 blocks large enough for the CTA-tiled
+  // kernels to pay (a 128 x 128 tile of C per CTA)
+  p->dp.dim = o.dense_layout == NRPF_DENSE_INSTANCE_MAJOR ||
+              (o.dense_layout == NRPF_DENSE_AUTO && im_ok && p->hp.nd >= NRPF_DENSE_IM_MIN);
   if (p->host_only) {
     *out = p;
     return NRPF_OK;
@@ -432,18 +453,28 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
       (rc = upload(p, h.bw_col, &d.bw_col)) || (rc = upload(p, h.unk_pos, &d.unk_pos)) ||
       (rc = upload(p, h.lu_lvl_ptr, &d.lu_lvl_ptr)) || (rc = upload(p, h.fw_lvl_ptr, &d.fw_lvl_ptr)) ||
       (rc = upload(p, h.bw_lvl_ptr, &d.bw_lvl_ptr)) || (rc = upload(p, h.schur_u, &d.schur_u)) ||
-      (rc = upload(p, h.schur_ent, &d.schur_ent)) || (rc = upload(p, h.schur_jmask, &d.schur_jmask))) {
+      (rc = upload(p, h.schur_ent, &d.schur_ent))) {
     pf_plan_destroy(p);
     return rc;
   }
   {
+    // instance-major dense block: it is zeroed before the Jacobian fill, so
+    // only the Schur tasks with products run (the others would write zeros
+    // and Jacobian entries already in place)
+    std::vector<int32_t> task_list;
+    std::vector<uint32_t> jmask;
+    for (size_t t = 0; t < h.schur_jmask.size(); ++t) {
+      if (d.dim && h.schur_task[4 * t + 2] == h.schur_task[4 * t + 3]) continue;
+      task_list.insert(task_list.end(), h.schur_task.begin() + 4 * t, h.schur_task.begin() + 4 * t + 4);
+      jmask.push_back(h.schur_jmask[t]);
+    }
     const int32_t* tasks = nullptr;
-    if ((rc = upload(p, h.schur_task, &tasks))) {
+    if ((rc = upload(p, task_list, &tasks)) || (rc = upload(p, jmask, &d.schur_jmask))) {
       pf_plan_destroy(p);
       return rc;
     }
     d.schur_task = reinterpret_cast<const int4*>(tasks);
-    d.n_schur = (int)(h.schur_task.size() / 4);
+    d.n_schur = (int)(task_list.size() / 4);
   }
   if (o.max_batch > 0 && (rc = ensure_capacity(p, o.max_batch))) {
     pf_plan_destroy(p);
@@ -477,6 +508,7 @@ int pf_plan_get_info(const pf_plan* p, pf_plan_info* info) {
   info->panel = h.kb;
   info->order_seed = (int)h.order_seed;
   info->order_key = h.order_key;
+  info->dense_layout = p->dp.dim ? NRPF_DENSE_INSTANCE_MAJOR : NRPF_DENSE_INTERLEAVED;
   return NRPF_OK;
 }
 

@@ -21,6 +21,7 @@ struct DevUpd {
 // Read-only plan arrays on the device (copied once by pf_plan_create).
 struct DevPlan {
   int n, m, s, nd, ndp, kb, mp;  // mp = s + ndp (rhs length incl. padding)
+  int dim;  // 1: instance-major dense block (FP32 LU; see dense_im.h), 0: interleaved
   int64_t NS, NLU;
   int nnzY;
   const int32_t* rowptr;   // [n+1]
@@ -91,6 +92,7 @@ struct DevState {
   int32_t* bad;     // [Bp] non-finite step detected
   SolveCtl* ctl;  // Newton loop control (one per workspace)
   const double2* yv;  // [nnzY] per-instance Ybus values (re, im), or null: the plan's shared values
+  const void* im_maps;  // host pointer to the workspace's DenseImMaps (instance-major plans), never read on the device
 };
 
 }  // namespace nrpf

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "../../include/nrpf.h"
+#include "dense_im.h"
 #include "device.h"
 #include "plan.h"
 #include "recorder.h"
@@ -21,6 +22,7 @@ struct pf_plan {
   std::vector<void*> plan_allocs;
   std::vector<void*> ws_allocs;
   int64_t* d_pattern_map = nullptr;  // CCS pattern -> LU element
+  nrpf::DenseImMaps im_maps{};       // TMA descriptors of the workspace (instance-major dense block)
   int64_t pattern_nnz = 0;
   nrpf::Recorder rec;
   // Newton loop as a graph: one iteration captured as the body of a WHILE

@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "dense_im.h"
 #include "device.h"
 #include "kernels.h"
 
@@ -39,12 +40,16 @@ __device__ __forceinline__ size_t dense_off(int r, int c, int ld, int lane) {
 }
 
 // offset of LU position p of lane `lane` within its tile's array (positions
-// >= NS are in the dense block)
+// >= NS are in the dense block: interleaved, grouped by four rows in FP32, or
+// instance-major when P.dim is set, lane l's block then at NS * 32 + l * ndp^2)
 template <typename T>
-__device__ __forceinline__ size_t lu_off(int64_t p, int64_t NS, int lane) {
+__device__ __forceinline__ size_t lu_off(const DevPlan& P, int64_t p, int lane) {
   constexpr int G = DenseGroup<T>::G;
-  if (G == 1 || p < NS) return (size_t)p * kTile + lane;
+  const int64_t NS = P.NS;
+  if (p < NS) return (size_t)p * kTile + lane;
   const int64_t q = p - NS;
+  if (P.dim) return (size_t)NS * kTile + (size_t)lane * (size_t)P.ndp * (size_t)P.ndp + (size_t)q;
+  if (G == 1) return (size_t)p * kTile + lane;
   return (size_t)NS * kTile + (size_t)(q & ~(int64_t)(G - 1)) * kTile + (size_t)lane * G + (size_t)(q & (G - 1));
 }
 
@@ -194,10 +199,10 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
           const T Wr = (T)ei * (T)yr + (T)fi * (T)yi;
           const T Wi = (T)fi * (T)yr - (T)ei * (T)yi;
           const T ik = (T)vinv[k * kTile + lane];
-          LU[lu_off<T>(jm.x, P.NS, lane)] = Wi;
-          if (jm.y >= 0) LU[lu_off<T>(jm.y, P.NS, lane)] = Wr * ik;
-          if (jm.z >= 0) LU[lu_off<T>(jm.z, P.NS, lane)] = -Wr;
-          if (jm.w >= 0) LU[lu_off<T>(jm.w, P.NS, lane)] = Wi * ik;
+          LU[lu_off<T>(P, jm.x, lane)] = Wi;
+          if (jm.y >= 0) LU[lu_off<T>(P, jm.y, lane)] = Wr * ik;
+          if (jm.z >= 0) LU[lu_off<T>(P, jm.z, lane)] = -Wr;
+          if (jm.w >= 0) LU[lu_off<T>(P, jm.w, lane)] = Wi * ik;
         }
       }
     }
@@ -223,10 +228,10 @@ __global__ void __launch_bounds__(32 * kMWarps) k_mismatch_jac(DevPlan P, DevSta
       const double vm2 = ei * ei + fi * fi;
       const double ivm = vinv[o];
       const double vm = vm2 * ivm;
-      LU[lu_off<T>(jm.x, P.NS, lane)] = (T)(-Qc - Bv * vm2);
-      if (jm.y >= 0) LU[lu_off<T>(jm.y, P.NS, lane)] = (T)(Pc * ivm + G * vm);
-      if (jm.z >= 0) LU[lu_off<T>(jm.z, P.NS, lane)] = (T)(Pc - G * vm2);
-      if (jm.w >= 0) LU[lu_off<T>(jm.w, P.NS, lane)] = (T)(Qc * ivm - Bv * vm);
+      LU[lu_off<T>(P, jm.x, lane)] = (T)(-Qc - Bv * vm2);
+      if (jm.y >= 0) LU[lu_off<T>(P, jm.y, lane)] = (T)(Pc * ivm + G * vm);
+      if (jm.z >= 0) LU[lu_off<T>(P, jm.z, lane)] = (T)(Pc - G * vm2);
+      if (jm.w >= 0) LU[lu_off<T>(P, jm.w, lane)] = (T)(Qc * ivm - Bv * vm);
     }
   }
   // NaN -> +inf so that the unsigned-integer max keeps it
@@ -355,6 +360,11 @@ __global__ void k_zero16(uint4* __restrict__ p, size_t n16, size_t stride16, int
   if (gate && *gate == 0) return;
   const uint4 z = make_uint4(0u, 0u, 0u, 0u);
   const size_t total = n16 * (size_t)tiles;
+  if (n16 == stride16) {  // the whole per-tile arrays: one contiguous range
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+      p[i] = z;
+    return;
+  }
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
     p[(i / n16) * stride16 + i % n16] = z;
 }
@@ -373,7 +383,7 @@ __global__ void k_set_ones(DevPlan P, DevState S, const int32_t* __restrict__ ga
   // (the refactorisation does not zero the dense block)
   for (int q = threadIdx.y; q < P.n_one * P.ndp; q += blockDim.y) {
     const int t = q / P.ndp, r = q % P.ndp;
-    LU[lu_off<T>(P.NS + (int64_t)(P.nd + t) * P.ndp + r, P.NS, lane)] = (T)(r == P.nd + t ? 1 : 0);
+    LU[lu_off<T>(P, P.NS + (int64_t)(P.nd + t) * P.ndp + r, lane)] = (T)(r == P.nd + t ? 1 : 0);
   }
   for (int t = threadIdx.y; t < P.n_one; t += blockDim.y) X[(size_t)(P.m + t) * kTile + lane] = (T)0;
 }
@@ -399,7 +409,6 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
   if (!tile_active(S, tile, lane)) return;
   T* __restrict__ LUb = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;  // tile base
   T* __restrict__ LU = LUb + lane;  // sparse positions (< NS): p * 32
-  const int64_t NS = P.NS;
   const int j = P.lu_cols[ci];
   const int u0 = P.col_upd_ptr[j], u1 = P.col_upd_ptr[j + 1];
   for (int u = u0; u < u1; ++u) {
@@ -409,8 +418,8 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
     const T* __restrict__ src = LU + (size_t)up.lsrc * kTile;
     int q = 0;
     for (; q + 4 <= up.llen; q += 4) {
-      const size_t o0 = lu_off<T>(dst[q], NS, lane), o1 = lu_off<T>(dst[q + 1], NS, lane);
-      const size_t o2 = lu_off<T>(dst[q + 2], NS, lane), o3 = lu_off<T>(dst[q + 3], NS, lane);
+      const size_t o0 = lu_off<T>(P, dst[q], lane), o1 = lu_off<T>(P, dst[q + 1], lane);
+      const size_t o2 = lu_off<T>(P, dst[q + 2], lane), o3 = lu_off<T>(P, dst[q + 3], lane);
       const T s0 = src[(size_t)q * kTile], s1 = src[(size_t)(q + 1) * kTile];
       const T s2 = src[(size_t)(q + 2) * kTile], s3 = src[(size_t)(q + 3) * kTile];
       const T a0 = LUb[o0], a1 = LUb[o1];
@@ -420,7 +429,7 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
       LUb[o2] = a2 - x * s2;
       LUb[o3] = a3 - x * s3;
     }
-    for (; q < up.llen; ++q) LUb[lu_off<T>(dst[q], NS, lane)] -= x * src[(size_t)q * kTile];
+    for (; q < up.llen; ++q) LUb[lu_off<T>(P, dst[q], lane)] -= x * src[(size_t)q * kTile];
   }
   const int dpj = P.dp[j];
   if (dpj >= 0) {
@@ -449,7 +458,7 @@ constexpr int kSchurWarps = 4;
 template <typename T>
 __global__ void __launch_bounds__(32 * kSchurWarps, sizeof(T) == 8 ? 7 : 1) k_schur(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;
-  __shared__ T acc[kSchurWarps][32][32];
+  __shared__ T acc[kSchurWarps][32][33];  // [row of the chunk][lane], padded: a row of one lane is read across the warp
   const int lane = threadIdx.x, w = threadIdx.y;
   const int t = blockIdx.x * kSchurWarps + w;
   const int tile = blockIdx.y;
@@ -457,7 +466,7 @@ __global__ void __launch_bounds__(32 * kSchurWarps, sizeof(T) == 8 ? 7 : 1) k_sc
   if (!tile_active(S, tile, lane)) return;
   T* __restrict__ LUb = reinterpret_cast<T*>(S.lu) + (size_t)tile * P.NLU * kTile;
   const T* __restrict__ LU = LUb + lane;  // sparse positions (< NS): p * 32
-  T(*a)[32] = acc[w];
+  T(*a)[33] = acc[w];
   const int4 task = P.schur_task[t];
   // A(i, j) = J(i, j) where J has an entry, else 0: the block is not zeroed
   // before the refactorisation; the Jacobian fill has written its entries
@@ -468,7 +477,7 @@ __global__ void __launch_bounds__(32 * kSchurWarps, sizeof(T) == 8 ? 7 : 1) k_sc
     const int nr = min(32, P.ndp - 32 * task.y);
 #pragma unroll 4
     for (int r = 0; r < 32; ++r)
-      a[r][lane] = (r < nr && (jm >> r & 1u)) ? LUb[lu_off<T>(col + r, P.NS, lane)] : (T)0;
+      a[r][lane] = (r < nr && (jm >> r & 1u)) ? LUb[lu_off<T>(P, col + r, lane)] : (T)0;
   } else {
 #pragma unroll
     for (int r = 0; r < 32; ++r) a[r][lane] = (T)0;
@@ -500,8 +509,26 @@ __global__ void __launch_bounds__(32 * kSchurWarps, sizeof(T) == 8 ? 7 : 1) k_sc
   }
   // every row of the chunk below the padded size is written back
   if constexpr (!kSeeded) {
-    // grouped FP32 block: rows 4g .. 4g+3 of the chunk are one 16-byte word
-    // per lane; A(i, j) minus the sum
+    if (P.dim) {
+      // instance-major block: instance l's 32 rows of column task.x are one
+      // contiguous 128-byte line, written by the whole warp (lane = row)
+      __syncwarp();
+      // (the block was zeroed and has received the Jacobian entries: the sums
+      // are subtracted in place)
+      const int nr = min(32, P.ndp - 32 * task.y);
+      float* __restrict__ col = LUb + (size_t)P.NS * kTile + (size_t)task.x * P.ndp + 32 * task.y + lane;
+      const size_t bstride = (size_t)P.ndp * (size_t)P.ndp;
+      if (lane < nr) {
+#pragma unroll 4
+        for (int l = 0; l < 32; ++l) {
+          float* q = col + (size_t)l * bstride;
+          *q -= a[lane][l];
+        }
+      }
+      return;
+    }
+    // FP32 grouped interleaved block: rows 4g .. 4g+3 of the chunk are one
+    // 16-byte word per lane; A(i, j) minus the sum
     float4* __restrict__ A4 = reinterpret_cast<float4*>(LUb + (size_t)P.NS * kTile);
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
@@ -520,7 +547,7 @@ __global__ void __launch_bounds__(32 * kSchurWarps, sizeof(T) == 8 ? 7 : 1) k_sc
     const int64_t col = P.NS + (int64_t)task.x * P.ndp + 32 * task.y;
     const int nr = min(32, P.ndp - 32 * task.y);
 #pragma unroll 4
-    for (int r = 0; r < nr; ++r) LUb[lu_off<T>(col + r, P.NS, lane)] = a[r][lane];
+    for (int r = 0; r < nr; ++r) LUb[lu_off<T>(P, col + r, lane)] = a[r][lane];
   }
 }
 
@@ -1006,7 +1033,7 @@ __global__ void k_lu_out(DevPlan P, DevState S, int B, const int64_t* __restrict
   const int b = tile * kTile + lane;
   if (b >= B) return;
   const T* LU = reinterpret_cast<const T*>(S.lu) + (size_t)tile * P.NLU * kTile;
-  out[(size_t)b * nnz + q] = (double)LU[lu_off<T>(map[q], P.NS, lane)];
+  out[(size_t)b * nnz + q] = (double)LU[lu_off<T>(P, map[q], lane)];
 }
 
 }  // namespace
@@ -1079,14 +1106,20 @@ void launch_prepare_lu(const DevPlan& P, const DevState& S, const int32_t* gate,
   // (both multiples of 128 bytes).  The dense block is left alone unless
   // `whole`: the Schur tasks then write every position of it.
   const size_t stride16 = (size_t)P.NLU * kTile * sizeof(T) / 16;
-  const size_t n16 = (whole || P.nd == 0) ? stride16 : (size_t)P.NS * kTile * sizeof(T) / 16;
+  // (instance-major dense block: zeroed too; its Schur tasks then subtract
+  // their products in place, and the chunks without products are skipped)
+  const size_t n16 = (whole || P.nd == 0 || P.dim) ? stride16 : (size_t)P.NS * kTile * sizeof(T) / 16;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   NRPF_LAUNCH(rec, K_ZERO, st,
               k_zero16<<<sms * 8, 256, 0, st>>>(reinterpret_cast<uint4*>(S.lu), n16, stride16, S.Bp / kTile, gate));
-  if (P.n_one > 0)
-    NRPF_LAUNCH(rec, K_ONES, st, k_set_ones<T><<<dim3(1, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate));
+  if (P.n_one > 0) {
+    if (sizeof(T) == 4 && P.dim)
+      launch_dense_im_set_ones(P, S, gate, st, rec);
+    else
+      NRPF_LAUNCH(rec, K_ONES, st, k_set_ones<T><<<dim3(1, S.Bp / kTile), dim3(32, 8), 0, st>>>(P, S, gate));
+  }
 }
 
 // one panel step of width KB at column k.  The column part of the panel
@@ -1150,6 +1183,12 @@ void launch_factor(const DevPlan& P, const DevState& S, const std::vector<int32_
   if (P.n_schur > 0)
     NRPF_LAUNCH(rec, K_SCHUR, st,
                 k_schur<T><<<grid2(P.n_schur, kSchurWarps, tiles), dim3(32, kSchurWarps), 0, st>>>(P, S, gate));
+  if constexpr (sizeof(T) == 4) {
+    if (P.dim) {
+      if (P.ndp > 0) launch_dense_im_factor(P, S, *reinterpret_cast<const DenseImMaps*>(S.im_maps), gate, st, rec);
+      return;
+    }
+  }
   for (int k = 0; k < P.ndp; k += P.kb) {
     if (P.kb == 4) launch_dense_step<T, 4>(P, S, k, P.ndp, P.ndp, gate, st, rec);
     else if (P.kb == 8) launch_dense_step<T, 8>(P, S, k, P.ndp, P.ndp, gate, st, rec);
@@ -1191,7 +1230,9 @@ void launch_solve(const DevPlan& P, const DevState& S, const std::vector<int32_t
       NRPF_LAUNCH(rec, K_FWD, st,
                   k_fwd_level<T><<<grid2(r1 - r0, 4, tiles), dim3(32, 4), 0, st>>>(P, S, r0, r1, gate));
   }
-  if (P.ndp > 0) {
+  if (sizeof(T) == 4 && P.dim) {
+    if (P.ndp > 0) launch_dense_im_solve(P, S, gate, st, rec);
+  } else if (P.ndp > 0) {
     const size_t smem = (size_t)P.ndp * kTile * sizeof(T);
     if (P.ndp % 8 == 0)
       launch_dense_solve_smem<T, 8>(P, S, gate, st, rec, smem);

@@ -13,6 +13,9 @@ from ._lib import check, lib
 
 _PREC = {"fp64": _lib.LU_FP64, "fp32": _lib.LU_FP32}
 _ORDER = {"amd": _lib.ORDER_AMD, "natural": _lib.ORDER_NATURAL}
+# dense-block storage: "auto" (instance-major for large FP32 blocks),
+# "interleaved", "instance_major"
+_LAYOUT = {"auto": 0, "interleaved": 1, "instance_major": 2}
 KERNEL_CLASSES = [lib.pf_kernel_class_name(i).decode() for i in range(16)]
 
 
@@ -41,7 +44,7 @@ class Plan:
 
     def __init__(self, n, rowptr, colidx, y_re, y_im, bus_type, lu_precision="fp64",
                  ordering="amd", dense_frac=0.0, panel=0, max_batch=0, host_only=False,
-                 order_tries=0):
+                 order_tries=0, dense_layout="auto"):
         self.n = int(n)
         self._rowptr = np.ascontiguousarray(rowptr, np.int32)
         self._colidx = np.ascontiguousarray(colidx, np.int32)
@@ -57,6 +60,7 @@ class Plan:
         opt.max_batch = int(max_batch)
         opt.host_only = int(bool(host_only))
         opt.order_tries = int(order_tries)
+        opt.dense_layout = _LAYOUT[dense_layout]
         h = C.c_void_p()
         check(lib.pf_plan_create(self.n, _lib._np_ptr(self._rowptr), _lib._np_ptr(self._colidx),
                                  _lib._np_ptr(self._yre), _lib._np_ptr(self._yim), _lib._np_ptr(self._bt),

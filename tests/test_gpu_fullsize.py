@@ -40,14 +40,15 @@ def _check(g, S, V0, Vg, itg, stg, idx, maxit, exact_iters):
 
 
 def test_mesh9000_fp32_full_batch_sampled():
-    """9,000 buses x 10,000 scenarios, FP32 LU with the default two-level panel
-    of 64 (the mixed-precision benchmark's configuration, about 206 GB of LU
-    workspace)."""
+    """9,000 buses x 10,000 scenarios, FP32 LU with the default dense block
+    (instance-major, factorised by the CTA-tiled kernels: the mixed-precision
+    benchmark's configuration, about 206 GB of LU workspace)."""
     pf = _pf()
     g = gridgen.make_grid("mesh9000_b10k")
     sc = gridgen.config_scenarios("mesh9000_b10k", g)
     S, V0 = sc.sbus(g), sc.v0_flat(g)
     with pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision="fp32") as p:
+        assert p.info["dense_layout"] == 2
         v, it, st = p.solve(torch.from_numpy(S).cuda(), torch.from_numpy(V0).cuda(), TOL, 10)
         Vg, itg, stg = v.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
     assert np.all(stg == 0)

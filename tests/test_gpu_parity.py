@@ -82,7 +82,14 @@ def test_mismatch_stage(name, B):
                                        ("mesh2000_b10k", 3, {"lu_precision": "fp32"}),
                                        ("mesh30_b64", 36, {"panel": 32}),
                                        ("mesh2000_b10k", 3, {"lu_precision": "fp32", "panel": 32}),
-                                       ("mesh2000_b10k", 2, {"lu_precision": "fp32", "panel": 64})])
+                                       ("mesh2000_b10k", 2, {"lu_precision": "fp32", "panel": 64}),
+                                       # instance-major dense block: ndp 64 (one last panel of 64),
+                                       # 320 (full, half and corner GEMM tiles), 384 (full tiles only)
+                                       ("mesh30_b64", 40, {"lu_precision": "fp32", "dense_layout": "instance_major"}),
+                                       ("mesh2000_b10k", 3, {"lu_precision": "fp32",
+                                                             "dense_layout": "instance_major"}),
+                                       ("mesh2000_b10k", 2, {"lu_precision": "fp32", "dense_layout": "instance_major",
+                                                             "dense_frac": 0.12})])
 def test_jacobian_and_factor_stage(name, B, kw):
     g, S, V0 = case(name, batch=B)
     V = perturbed(V0, seed=4)
@@ -115,7 +122,12 @@ def test_jacobian_and_factor_stage(name, B, kw):
                                        ("mesh30_b64", 40, {"lu_precision": "fp32", "panel": 32}),
                                        ("mesh2000_b10k", 8, {"lu_precision": "fp32", "panel": 32}),
                                        ("mesh30_b64", 33, {"panel": 64}),
-                                       ("mesh2000_b10k", 8, {"lu_precision": "fp32", "panel": 64})])
+                                       ("mesh2000_b10k", 8, {"lu_precision": "fp32", "panel": 64}),
+                                       ("mesh30_b64", 45, {"lu_precision": "fp32", "dense_layout": "instance_major"}),
+                                       ("mesh2000_b10k", 8, {"lu_precision": "fp32",
+                                                             "dense_layout": "instance_major"}),
+                                       ("mesh2000_b10k", 8, {"lu_precision": "fp32", "dense_layout": "instance_major",
+                                                             "dense_frac": 0.12})])
 def test_linear_solve_stage(name, B, kw):
     g, S, V0 = case(name, batch=B)
     V = perturbed(V0, seed=5)
@@ -196,6 +208,27 @@ def test_edge_cases():
         assert pf.lib.pf_solve_batch(p._h, 1, None, None, float("nan"), 10, None, None, None, None) == -1
 
 
+def test_instance_major_edge_cases():
+    """Instance-major FP32 dense block: a non-finite injection fails its own
+    instance only, an instance that starts at the solution takes no update,
+    and maxit = 0 reports every instance at its limit."""
+    g, S, V0 = case("mesh2000_b10k", batch=36)
+    Vo, ito, sto = _oracle_solve(g, S[:2], V0[:2], tol=1e-12, maxit=20)
+    with _plan(g, lu_precision="fp32", dense_layout="instance_major") as p:
+        assert p.info["dense_layout"] == 2
+        Sb = S.copy()
+        Sb[33, 17] = np.nan
+        V0b = V0.copy()
+        V0b[:2] = Vo
+        v, it, st = p.solve(_dev(Sb), _dev(V0b), TOL, 20)
+        st, it = st.cpu().numpy(), it.cpu().numpy()
+        assert st[33] == 2 and it[33] == 0
+        assert np.all(np.delete(st, 33) == 0)
+        assert np.all(it[:2] == 0)
+        v, it, st = p.solve(_dev(S), _dev(V0), TOL, 0)
+        assert np.all(it.cpu().numpy() == 0) and np.all(st.cpu().numpy() == 1)
+
+
 def test_singular_instance_reports_failure():
     """An instance whose Jacobian is singular (a PQ bus with zero voltage)
     stops with status 2 while the rest of the batch converges."""
@@ -219,14 +252,16 @@ def test_plan_reuse_and_capacity_growth():
         assert p.info["capacity"] >= 64
 
 
-@pytest.mark.parametrize("name,B,panel", [("mesh30_b64", 64, 0), ("mesh2000_b10k", 40, 0),
-                                          ("mesh2000_b10k", 40, 32), ("mesh2000_b10k", 40, 64)])
-def test_mixed_precision_lu(name, B, panel):
+@pytest.mark.parametrize("name,B,panel,layout", [("mesh30_b64", 64, 0, "auto"), ("mesh2000_b10k", 40, 0, "auto"),
+                                                 ("mesh2000_b10k", 40, 32, "auto"), ("mesh2000_b10k", 40, 64, "auto"),
+                                                 ("mesh30_b64", 64, 0, "instance_major"),
+                                                 ("mesh2000_b10k", 70, 0, "instance_major")])
+def test_mixed_precision_lu(name, B, panel, layout):
     """FP32 LU + FS/BS, FP64 mismatch/update: same statuses, same tolerance,
-    a few more iterations at most (default panel, and the two-level panels of
-    32 and 64 factorised in steps of 16)."""
+    a few more iterations at most (default panel, the two-level panels of
+    32 and 64 factorised in steps of 16, and the instance-major dense block)."""
     g, S, V0 = case(name, batch=B)
-    with _plan(g, lu_precision="fp32", panel=panel) as p:
+    with _plan(g, lu_precision="fp32", panel=panel, dense_layout=layout) as p:
         v, it, st = p.solve(_dev(S), _dev(V0), TOL, 20)
         Vg, itg, stg = v.cpu().numpy(), it.cpu().numpy(), st.cpu().numpy()
     idx = list(range(0, B, max(1, B // 10)))

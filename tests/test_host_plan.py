@@ -242,3 +242,57 @@ def test_orderings_of_both_keys_give_closed_patterns():
         keys.add(info["order_key"])
         assert info["dense_dim"] > 0
     assert keys == {0, 1}
+
+
+def test_dense_layout_selection_and_validation():
+    """The instance-major dense block is chosen by default for FP32 LU plans
+    whose dense block has at least NRPF_DENSE_IM_MIN (512) unknowns and panel
+    64, and never for FP64 plans; asking for it with FP64 LU or another panel
+    width is an invalid argument; its block is padded to a multiple of 64."""
+    pf = _lib()
+    g = gridgen.make_grid("mesh2000_b10k")
+    kw = dict(host_only=True, order_tries=1)
+    p = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision="fp32", **kw)
+    assert p.info["dense_dim"] < 512 and p.info["dense_layout"] == 1  # 2,000 buses: interleaved
+    p = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision="fp32",
+                              dense_layout="instance_major", **kw)
+    assert p.info["dense_layout"] == 2 and p.info["dense_pad"] % 64 == 0 and p.info["panel"] == 64
+    # a larger dense block (smaller dense_frac) switches the default
+    p = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision="fp32", dense_frac=0.02, **kw)
+    assert p.info["dense_dim"] >= 512 and p.info["dense_layout"] == 2
+    p = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision="fp64", dense_frac=0.02, **kw)
+    assert p.info["dense_layout"] == 1
+    p = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision="fp32", dense_frac=0.02,
+                              panel=16, **kw)
+    assert p.info["dense_layout"] == 1
+    for bad in (dict(lu_precision="fp64", dense_layout="instance_major"),
+                dict(lu_precision="fp32", dense_layout="instance_major", panel=32)):
+        with pytest.raises(pf.NrpfError, match="invalid argument"):
+            pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, **bad, **kw)
+
+
+def test_instance_major_update_accounting_matches_lu_arithmetic():
+    """bench.py's flop count of the instance-major trailing updates (k_im_gemm:
+    per outer panel of 128, the block right of and below it with depth 128)
+    plus the work of the diagonal and panel kernels (64-wide steps, the second
+    step of an outer panel first taking its left-looking product with the
+    first) equals the multiply-adds of a right-looking LU without pivoting."""
+    import importlib.util
+    import pathlib
+    spec = importlib.util.spec_from_file_location("bench", pathlib.Path(__file__).parent.parent / "bench.py")
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    diag = sum((63 - c) + (63 - c) ** 2 for c in range(64))  # 64 x 64 LU: scaling + rank-1 updates
+    row_solve = sum(c + 1 for c in range(64))                # x U11 = a: c subtractions + 1 scaling
+    col_solve = sum(63 - q for q in range(63))               # L11 y = a (unit lower)
+    for n in (64, 320, 384, 2176):
+        total = sum((n - k - 1) + (n - k - 1) ** 2 for k in range(n))
+        gemm = sum(r * c * d for L in bench.dense_update_launches_im(n) for r, c, d in L)
+        other = 0
+        for k in range(0, n, 128):
+            nr0 = n - k - 64
+            other += diag + nr0 * (row_solve + col_solve)
+            if n - k >= 128:
+                nr1 = n - k - 128
+                other += 64 ** 3 + diag + nr1 * (2 * 64 * 64 + row_solve + col_solve)
+        assert gemm + other == total, n
