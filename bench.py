@@ -4,9 +4,13 @@
 A step is one pf_solve_batch over the whole batch of the workload (every NR
 iteration: mismatch + Jacobian refill, sparse + dense LU refactor, FS/BS,
 update, until max|F| < 1e-8 p.u. or maxit) with inputs resident in HBM.
-Default workload: 2,000-bus meshed synthetic grid, 10,000 load scenarios,
-plain FP64, flat start, tol 1e-8, maxit 10 (``--config`` / ``--lu`` select
-other workloads).  Prints one JSON line.
+Default workload: the 9,000-bus meshed synthetic grid, 10,000 load scenarios,
+the mixed-precision form (LU refactor and FS/BS in FP32; mismatch, update and
+convergence test in FP64), flat start, tol 1e-8, maxit 10.  The same line
+carries the 2,000-bus workload in plain FP64 and with FP32 LU, the learned
+warm start, and plain FP64 on a subset of the 9,000-bus batch, each with its
+own oracle comparison (``--config`` / ``--lu`` select a single workload).
+Prints one JSON line.
 
 Multi-GPU (torchrun): every rank solves its own batch (weak scaling, no data
 exchange); barrier + max-over-ranks timing.
@@ -56,18 +60,26 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="mesh2000_b10k",
+    ap.add_argument("--config", default="mesh9000_b10k",
                     choices=list(gridgen.CONFIGS) + ["feeders256x100", "warmstart2000", "n1_2000"])
     ap.add_argument("--train-samples", type=int, default=200000)
     ap.add_argument("--train-steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=0, help="override the batch size (0 = the workload's)")
-    ap.add_argument("--lu", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--lu", default=None, choices=["fp64", "fp32"],
+                    help="LU precision (default: fp32 for the 9,000-bus workload, fp64 otherwise)")
     ap.add_argument("--maxit", type=int, default=MAXIT)
     ap.add_argument("--dense-frac", type=float, default=0.0, help="0 = the library's default for the precision")
     ap.add_argument("--panel", type=int, default=0, help="0 = the library's default for the precision")
+    ap.add_argument("--dense-layout", default="auto", choices=["auto", "interleaved", "instance_major"],
+                    help="storage of the dense block (auto: instance-major for large FP32 blocks)")
     ap.add_argument("--chunk", type=int, default=0,
                     help="instances per chunk of the end-to-end host solve (0 = about a quarter of the batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: skip the 2,000-bus, warm-start and FP64-subset keys")
+    ap.add_argument("--roofline-steps", type=int, default=0,
+                    help="steps of the per-launch-timed roofline pass (0: all K steps, at most 4 on the "
+                         "9,000-bus workload)")
     ap.add_argument("--time-all", action="store_true",
                     help="diagnostic: CUDA-event timing of every kernel class (adds two events per launch)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -124,69 +136,85 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 # ---------------------------------------------------------------------------
+# one oracle solve on grids above this size takes longer than the whole CPU
+# budget of a bench line (about 100 s on one Grace core for 9,000 buses): the
+# sample is then one round of one instance per core, without a calibration run
+ORACLE_ROUND_ONLY_BUSES = 4000
+
+
 def _oracle_cases(task):
     """Oracle Newton solves of instances with their own branch sets (one
-    process of the per-instance-admittance sample)."""
+    process of the per-instance-admittance sample): (V, iters, status)."""
     from oracle import nrpf
     n, f, t, r, x, b, bus_type, ins, S, V0 = task
-    st = []
+    out = []
     for keep, s, v0 in zip(ins, S, V0):
         Y = nrpf.make_ybus(n, f[keep], t[keep], r[keep], x[keep], b[keep])
-        st.append(nrpf.newton(Y, s, v0, bus_type, TOL, MAXIT)[2])
-    return st
+        out.append(nrpf.newton(Y, s, v0, bus_type, TOL, MAXIT))
+    return (np.array([o[0] for o in out]), np.array([o[1] for o in out]), np.array([o[2] for o in out]))
+
+
+def compare_with_oracle(Vg, itg, stg, Vo, ito, sto):
+    """The GPU's results against the FP64 oracle's on the same instances:
+    statuses, max |V| and angle differences, Newton-iteration difference
+    (GPU minus oracle)."""
+    ok = (sto == 0) & (stg == 0)
+    Vs = Vg[ok]
+    dvm = np.abs(np.abs(Vs) - np.abs(Vo[ok]))
+    dth = np.abs(np.angle(Vs * np.conj(Vo[ok])))
+    dit = itg[ok].astype(int) - ito[ok].astype(int)
+    return {"instances": int(len(sto)), "same_status": bool(np.array_equal(stg, sto)),
+            "max_abs_dv": float(np.max(np.abs(Vs - Vo[ok]), initial=0.0)),
+            "max_abs_dvm": float(np.max(dvm, initial=0.0)), "max_abs_dtheta": float(np.max(dth, initial=0.0)),
+            "max_iter_diff": int(np.max(np.abs(dit), initial=0)),
+            "mean_iter_diff": float(np.mean(dit)) if dit.size else 0.0,
+            "oracle_iters_mean": float(np.mean(ito)), "tolerance": "|dV| <= 1e-6 p.u., |dtheta| <= 1e-6 rad"}
 
 
 def oracle_sample(g, S, V0, seconds, cores, ins=None, gpu=None):
     """Time the CPU oracle on a bounded sample of the workload: a first
     calibration run sizes the sample to about `seconds` of work on `cores`
-    processes.  ins [B, nbr] (optional): per-instance branch sets, each
-    instance then gets its own admittance matrix."""
+    processes (grids above ORACLE_ROUND_ONLY_BUSES: one round of one instance
+    per core).  ins [B, nbr] (optional): per-instance branch sets, each
+    instance then gets its own admittance matrix.  gpu = (V, iters, status)
+    of the GPU on the whole batch: the sample's oracle results are compared
+    with them ("vs_oracle")."""
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     from oracle import nrpf
     B = S.shape[0]
     if ins is None:
         Y = nrpf.make_ybus(g.n, g.f, g.t, g.r, g.x, g.b)
-        run = lambda k, w: nrpf.newton_batch(Y, S[:k], V0[:k], g.bus_type, TOL, MAXIT, workers=w)[2]
+        run = lambda k, w: nrpf.newton_batch(Y, S[:k], V0[:k], g.bus_type, TOL, MAXIT, workers=w)
     else:
         import multiprocessing as mp
 
         def run(k, w):
             if w <= 1 or k < 2:
-                return np.array(_oracle_cases((g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, ins[:k], S[:k], V0[:k])))
+                return _oracle_cases((g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, ins[:k], S[:k], V0[:k]))
             parts = np.array_split(np.arange(k), min(w, k))
             tasks = [(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, ins[p], S[p], V0[p]) for p in parts]
             with mp.get_context("spawn").Pool(len(tasks)) as pool:
-                return np.concatenate([np.array(o) for o in pool.map(_oracle_cases, tasks)])
+                res = pool.map(_oracle_cases, tasks)
+            return tuple(np.concatenate([r[i] for r in res]) for i in range(3))
+    if g.n > ORACLE_ROUND_ONLY_BUSES:
+        size = min(cores, B)
+    else:
+        t0 = time.perf_counter()
+        run(1, 1)
+        t1 = max(time.perf_counter() - t0, 1e-4)
+        size = min(B, int(max(cores, min(B, seconds * cores / t1))))
     t0 = time.perf_counter()
-    run(1, 1)
-    t1 = max(time.perf_counter() - t0, 1e-4)
-    size = int(max(cores, min(B, seconds * cores / t1)))
-    size = min(size, B)
-    t0 = time.perf_counter()
-    st = run(size, cores)
+    Vo, ito, sto = run(size, cores)
     dt = time.perf_counter() - t0
-    conv = int(np.sum(st == 0))
+    conv = int(np.sum(sto == 0))
     what = "instances (own admittance matrix each)" if ins is not None else "scenarios"
-    out = {"value": conv / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    out = {"value": conv / dt, "unit": UNIT, "cores": min(cores, size), "kind": "oracle",
            "sample": f"first {size} of {B} {what}, scipy SuperLU per Newton step, "
-                     f"{cores} spawn processes, {dt:.1f} s"}
+                     f"{min(cores, size)} spawn processes, {dt:.1f} s"}
     if gpu is not None:
-        # the GPU's results on (the first few of) the same instances against
-        # the oracle's, solved again one by one with their voltages kept
         Vg, itg, stg = gpu
-        k = min(size, 8)
-        Y = None if ins is not None else nrpf.make_ybus(g.n, g.f, g.t, g.r, g.x, g.b)
-        dv, dit, same = 0.0, 0, True
-        for b in range(k):
-            Yb = Y if Y is not None else nrpf.make_ybus(g.n, g.f[ins[b]], g.t[ins[b]], g.r[ins[b]], g.x[ins[b]],
-                                                        g.b[ins[b]])
-            Vo, ito, sto = nrpf.newton(Yb, S[b], V0[b], g.bus_type, TOL, MAXIT)
-            same = same and int(stg[b]) == int(sto)
-            if sto == 0:
-                dv = max(dv, float(np.max(np.abs(Vg[b] - Vo))))
-                dit = max(dit, abs(int(itg[b]) - int(ito)))
-        out["vs_oracle"] = {"instances": k, "same_status": same, "max_abs_dv": dv, "max_iter_diff": dit}
+        out["vs_oracle"] = compare_with_oracle(Vg[:size], itg[:size], stg[:size], Vo, ito, sto)
     return out
 
 
@@ -260,6 +288,22 @@ def run_reference(args):
             vals.append(last["value"])
         return statistics.mean(vals), last
 
+    if any(case[0].n > ORACLE_ROUND_ONLY_BUSES for case in cases):
+        # a single oracle solve of this grid takes about 100 s on one core:
+        # one round of one instance per core stands for the K steps (and the
+        # warm-up is the spawn of the processes inside it)
+        t0 = time.perf_counter()
+        v, last = one(per_step)
+        dt = time.perf_counter() - t0
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": name, "batch": batch, "tol": TOL, "maxit": MAXIT,
+                                                "reference_rounds": 1},
+                "cpu_baseline": dict(last, value=v, sample=last["sample"] + "; one round stands for the K steps"),
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     for _ in range(args.warmup):
         one(min(per_step, 2.0))
     vals = []
@@ -453,10 +497,16 @@ def run_feeders(args):
 
 
 def run_warmstart(args):
+    print(json.dumps(warmstart_measure(args, args.steps, args.warmup)), flush=True)
+
+
+def warmstart_measure(args, steps, warmup):
     """Learned warm start on the 2,000-bus grid: 200,000 solver-made solutions
     (scenario seeds 2, 3, ...) train the 4000-1024-1024-3998 network; the
     10,000 held-out scenarios (seed 1, the 2,000-bus workload) are then solved
-    from its guesses and from flat start, NR to 1e-8 p.u. with fallback."""
+    from its guesses and from flat start, NR to 1e-8 p.u. with fallback (a
+    result that did not converge or sits on a low-voltage root is re-solved
+    from flat start).  Returns the JSON line as a dict."""
     import torch
 
     import paper_2101_02270_gb300 as pf
@@ -493,9 +543,9 @@ def run_warmstart(args):
     gen = torch.Generator(device=dev).manual_seed(0)
     loss = None
     t0 = time.perf_counter()
-    steps = args.train_steps
-    for step in range(steps):
-        lr = 1e-3 * (0.5 * (1 + np.cos(np.pi * step / steps))) + 2e-5
+    train_steps = args.train_steps
+    for step in range(train_steps):
+        lr = 1e-3 * (0.5 * (1 + np.cos(np.pi * step / train_steps))) + 2e-5
         idx = torch.randint(0, X.shape[0], (1024,), device=dev, generator=gen)
         loss = net.train_step(X[idx].contiguous(), T[idx].contiguous(), lr=lr, wd=1e-4)
     torch.cuda.synchronize()
@@ -510,16 +560,16 @@ def run_warmstart(args):
     stream = torch.cuda.current_stream()
 
     def timed(fn):
-        for _ in range(max(args.warmup, 1)):
+        for _ in range(max(warmup, 1)):
             fn()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             r = fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps, r
+        return e0.elapsed_time(e1) / steps, r
 
     clocks = ClockSampler(dev.index or 0)
     clocks.start()
@@ -532,9 +582,9 @@ def run_warmstart(args):
     # any flat-start fallback) plus the network's per guess: features, v0 and,
     # per chunk of bmax instances, input scaling + three GEMMs + output scaling
     # (the counters also saw the warm-up calls: scale to the timed ones)
-    calls = max(args.warmup, 1) + args.steps
-    per_call = sum(v[0] for v in prof.values()) / calls + 2 + 5 * -(-S_np.shape[0] // net.bmax)
-    launches = int(round(per_call * args.steps))
+    calls = max(warmup, 1) + steps
+    per_call = sum(v[0] for v in prof.values()) / calls + 3 + 5 * -(-S_np.shape[0] // net.bmax)
+    launches = int(round(per_call * steps))
     ms_flat32, (vf32, itf32, stf32) = timed(lambda: plan32.solve(Sh, Vh, TOL, 20))
     ms_warm32, (vw32, itw32, stw32, fb32) = timed(lambda: ws32.solve(Sh, Vh, TOL, 20))
     clk = clocks.stop()
@@ -561,28 +611,28 @@ def run_warmstart(args):
     ms_e2e, _ = timed(e2e)
     e2e_value = int((st_pin == 0).sum()) / (ms_e2e / 1e3)
     dv = float((vw - vf).abs().max().item())
-    # oracle check of a sample of warm-started results
-    from oracle import nrpf
-    Y = nrpf.make_ybus(g.n, g.f, g.t, g.r, g.x, g.b)
-    idx = np.random.default_rng(0).choice(B, 8, replace=False)
-    Vo, ito, sto = nrpf.newton_batch(Y, S_np[idx], V0_np[idx], g.bus_type, TOL, MAXIT)
-    vw_np = vw.cpu().numpy()
-    d_or = float(np.max(np.abs(vw_np[idx] - Vo)))
+    # the warm-started results against the FP64 oracle's flat-start solutions
+    # on sampled held-out scenarios (iteration difference: saved iterations
+    # show as negative numbers)
+    idx = sample_indices(B)
+    vo64 = vs_oracle(g, S_np, V0_np, vw.cpu().numpy(), itw.cpu().numpy(), stw.cpu().numpy(), idx, MAXIT)
+    vo32 = vs_oracle(g, S_np, V0_np, vw32.cpu().numpy(), itw32.cpu().numpy(), stw32.cpu().numpy(), idx, MAXIT)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": steps, "warmup": warmup,
         "ms_per_step": ms_warm64, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 (NR) + bf16 (MLP)", "data": "synthetic",
         "config": {"workload": "warmstart2000", "buses": g.n, "held_out": B, "train_samples": nchunks * chunk,
-                   "train_steps": steps, "mlp": [2 * g.n, 1024, 1024, 2 * nns], "tol": TOL},
+                   "train_steps": train_steps, "mlp": [2 * g.n, 1024, 1024, 2 * nns], "tol": TOL},
         "warm_fp64": {"flows_s": value, "ms": ms_warm64, "iters_mean": float(itw.float().mean()),
                       "fallbacks": int(fb.sum()), "converged": conv},
         "flat_fp64": {"flows_s": int((stf == 0).sum()) / (ms_flat64 / 1e3), "ms": ms_flat64,
                       "iters_mean": float(itf.float().mean())},
         "warm_fp32lu": {"flows_s": int((stw32 == 0).sum()) / (ms_warm32 / 1e3), "ms": ms_warm32,
-                        "iters_mean": float(itw32.float().mean()), "fallbacks": int(fb32.sum())},
+                        "iters_mean": float(itw32.float().mean()), "fallbacks": int(fb32.sum()),
+                        "vs_oracle": vo32},
         "flat_fp32lu": {"flows_s": int((stf32 == 0).sum()) / (ms_flat32 / 1e3), "ms": ms_flat32,
                         "iters_mean": float(itf32.float().mean())},
-        "max_dv_warm_vs_flat": dv, "max_dv_warm_vs_oracle_sample": d_or,
+        "max_dv_warm_vs_flat": dv, "vs_oracle": vo64,
         "training": {"generate_s": round(gen_s, 2), "train_s": round(train_s, 2), "final_loss": final_loss},
         "clocks": clk, "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(2 * S_pin.nbytes),
@@ -590,10 +640,14 @@ def run_warmstart(args):
         "roofline": whole_solve_roofline([(plan64.info, 8, int(itw.sum()))], ms_warm64,
                                          "the warm-started FP64 solve (its dense update is FP64-bound)"),
     }
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.config == "warmstart2000":
         line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1)
         line["cpu_baseline"]["sample"] += " (flat start: the oracle has no network)"
-    print(json.dumps(line), flush=True)
+    plan64.close()
+    plan32.close()
+    net.close()
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_small(args):
@@ -673,22 +727,50 @@ def run_small(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
+def vs_oracle(g, S, V0, Vg, itg, stg, idx, maxit):
+    """The GPU's results on the sampled instances idx against the FP64 oracle
+    (oracle/nrpf.py), each re-solved from the same start in spawn processes."""
+    from oracle import nrpf
+    idx = np.asarray(idx)
+    Y = nrpf.make_ybus(g.n, g.f, g.t, g.r, g.x, g.b)
+    cores = os.cpu_count() or 1
+    Vo, ito, sto = nrpf.newton_batch(Y, S[idx], V0[idx], g.bus_type, TOL, maxit, workers=min(len(idx), cores))
+    out = compare_with_oracle(Vg[idx], itg[idx], stg[idx], Vo, ito, sto)
+    out["sample"] = "instances " + ",".join(str(int(i)) for i in idx)
+    return out
+
+
+def sample_indices(B, k=8, seed=0):
+    """First, middle and last instance plus seeded random ones."""
+    pick = {0, B // 2, B - 1}
+    rng = np.random.default_rng(seed)
+    while len(pick) < min(k, B):
+        pick.add(int(rng.integers(B)))
+    return sorted(pick)
+
+
+def dense_update_launches_im(ndp):
+    """The k_im_gemm launches of one instance-major dense refactor: per outer
+    panel of 128 at column k, the trailing block [k+128, ndp)^2 with depth
+    128 (the second 64-wide step's left-looking products are counted with the
+    diagonal and panel kernels)."""
+    return [[(ndp - k - 128, ndp - k - 128, 128)] for k in range(0, ndp, 128) if ndp - k - 128 > 0]
+
+
+def measure_mesh(args, pf, name, lu, steps, warmup, dev, rank=0, world=1, with_cpu=True, batch=None,
+                 roof_steps=None, e2e=True):
+    """One meshed-grid workload: K timed pf_solve_batch steps (graph-ended
+    Newton loop, inputs in HBM), a per-launch-timed pass for the dominant
+    kernel's roofline, the end-to-end rate through pf_solve_batch_host, the
+    oracle comparison on sampled instances and (optionally) the CPU
+    baselines.  Returns the JSON line as a dict."""
+    import ctypes as C
+
     import torch
     import torch.distributed as dist
 
-    import ctypes as C
+    from paper_2101_02270_gb300.solver import KERNEL_CLASSES
 
-    import paper_2101_02270_gb300 as pf
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local)
-    name = args.config
     n1 = name == "n1_2000"  # static N-1: every connected single outage x load levels
     g = gridgen.make_grid("mesh2000_b10k" if n1 else name)
     ins = None
@@ -697,20 +779,20 @@ def run_ours(args):
         _, _, ins, S_np = gridgen.n1_batch(g, levels=tuple(l * (1 + 0.01 * rank) for l in gridgen.N1_LEVELS))
         V0_np = np.broadcast_to(g.v_set.astype(np.complex128), S_np.shape).copy()
     else:
-        sc = rank_scenarios(name, g, rank, batch=args.batch or None)
+        sc = rank_scenarios(name, g, rank, batch=batch or args.batch or None)
         S_np, V0_np = sc.sbus(g), sc.v0_flat(g)
     B = S_np.shape[0]
     S = torch.from_numpy(S_np).to(dev)
     V0 = torch.from_numpy(V0_np).to(dev)
     t0 = time.perf_counter()
-    plan = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision=args.lu,
-                                 dense_frac=args.dense_frac, panel=args.panel, max_batch=B)
+    plan = pf.Plan.from_branches(g.n, g.f, g.t, g.r, g.x, g.b, g.bus_type, lu_precision=lu,
+                                 dense_frac=args.dense_frac, panel=args.panel, max_batch=B,
+                                 dense_layout=args.dense_layout if lu == "fp32" else "auto")
     plan_ms = 1e3 * (time.perf_counter() - t0)
-    # N-1: each instance lists its outaged branch; the admittances are built
-    # on the device from the plan's base values
     out_np = np.argmin(ins, axis=1).astype(np.int32)[:, None] if n1 else None
     Od = torch.from_numpy(out_np).to(dev) if n1 else None
     info = plan.info
+    im = info["dense_layout"] == 2
     fp64_peak, fp32_peak = pf._lib.fma_peak(C.c_void_p(torch.cuda.current_stream().cuda_stream))
     out = (torch.empty((B, g.n), dtype=torch.complex128, device=dev),
            torch.empty(B, dtype=torch.int32, device=dev), torch.empty(B, dtype=torch.uint8, device=dev))
@@ -721,7 +803,7 @@ def run_ours(args):
             return plan.solve_outages(Od, S, V0, TOL, args.maxit, out=out)
         return plan.solve(S, V0, TOL, args.maxit, out=out)
 
-    for _ in range(max(args.warmup, 0)):
+    for _ in range(max(warmup, 0)):
         step()
     torch.cuda.synchronize()
 
@@ -730,159 +812,218 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev.index or 0)
     clocks.start()
     time.sleep(0.3)
-    from paper_2101_02270_gb300.solver import KERNEL_CLASSES
     plan.profile_start([])  # launch counts only: the Newton loop runs as a graph
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     barrier()
     ms = e0.elapsed_time(e1)
     counts = plan.profile_read()
     clk = clocks.stop()
-    # per-kernel device times: the same K steps again with CUDA events around
+    # per-kernel device times: timed steps again with CUDA events around
     # every launch of the timed classes, on the launch stream (the loop then
-    # runs from the host; the kernels and their work are the same)
+    # ends from the host; the kernels and their work are the same)
+    rsteps = steps if roof_steps is None else max(1, min(steps, roof_steps))
     plan.profile_start(KERNEL_CLASSES if args.time_all else ["dense_update"])
-    for _ in range(args.steps):
+    for _ in range(rsteps):
         step()
     prof = plan.profile_read()
     plan.profile_start([])  # per-launch timing off again: later solves run the graph loop
     iters = out[1].cpu().numpy()
     status = out[2].cpu().numpy()
+    Vg = out[0].cpu().numpy()
     conv = int(np.sum(status == 0))
     ms_max, conv_all = combine_ranks(ms, conv, dev)
-    value = conv_all * args.steps / (ms_max / 1e3)
+    value = conv_all * steps / (ms_max / 1e3)
     launches = int(sum(v[0] for v in counts.values()))
 
     # ---- end to end through the public API with host buffers ----
     # (pf_solve_batch_host: chunks of the batch copied in and out on the
     # plan's copy streams while the neighbouring chunks are solved)
-    S_h = torch.from_numpy(S_np).pin_memory()
-    V0_h = torch.from_numpy(V0_np).pin_memory()
-    V_h = torch.empty((B, g.n), dtype=torch.complex128).pin_memory()
-    it_h = torch.empty(B, dtype=torch.int32).pin_memory()
-    st_h = torch.empty(B, dtype=torch.uint8).pin_memory()
-    if n1:
-        # the outage lists travel with the injections: copies in, solve, copies out
-        O_h = torch.from_numpy(out_np).pin_memory()
-        Sd, Vd, Odd = torch.empty_like(S), torch.empty_like(V0), torch.empty_like(Od)
+    e2e_line = None
+    if e2e:
+        S_h = torch.from_numpy(S_np).pin_memory()
+        V0_h = torch.from_numpy(V0_np).pin_memory()
+        V_h = torch.empty((B, g.n), dtype=torch.complex128).pin_memory()
+        it_h = torch.empty(B, dtype=torch.int32).pin_memory()
+        st_h = torch.empty(B, dtype=torch.uint8).pin_memory()
+        if n1:
+            # the outage lists travel with the injections: copies in, solve, copies out
+            O_h = torch.from_numpy(out_np).pin_memory()
+            Sd, Vd, Odd = torch.empty_like(S), torch.empty_like(V0), torch.empty_like(Od)
 
-        def e2e_step():
-            Odd.copy_(O_h, non_blocking=True)
-            Sd.copy_(S_h, non_blocking=True)
-            Vd.copy_(V0_h, non_blocking=True)
-            v, it, st = plan.solve_outages(Odd, Sd, Vd, TOL, args.maxit, out=out)
-            V_h.copy_(v, non_blocking=True)
-            it_h.copy_(it, non_blocking=True)
-            st_h.copy_(st, non_blocking=True)
-    else:
-        def e2e_step():
-            plan.solve_host(S_h, V0_h, TOL, args.maxit, out=(V_h, it_h, st_h), chunk=args.chunk)
-    e2e_step()  # staging warm-up
-    barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    barrier()
-    ms_e2e, conv_e2e = combine_ranks(e0.elapsed_time(e1), int(np.sum(st_h.numpy() == 0)), dev)
-    e2e_value = conv_e2e * args.steps / (ms_e2e / 1e3)
-    h2d = 2 * B * g.n * 16 + (out_np.nbytes if n1 else 0)
-    d2h = B * g.n * 16 + B * 4 + B
+            def e2e_step():
+                Odd.copy_(O_h, non_blocking=True)
+                Sd.copy_(S_h, non_blocking=True)
+                Vd.copy_(V0_h, non_blocking=True)
+                v, it, st = plan.solve_outages(Odd, Sd, Vd, TOL, args.maxit, out=out)
+                V_h.copy_(v, non_blocking=True)
+                it_h.copy_(it, non_blocking=True)
+                st_h.copy_(st, non_blocking=True)
+        else:
+            def e2e_step():
+                plan.solve_host(S_h, V0_h, TOL, args.maxit, out=(V_h, it_h, st_h), chunk=args.chunk)
+        e2e_step()  # staging warm-up
+        barrier()
+        e0.record(stream)
+        for _ in range(steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        ms_e2e, conv_e2e = combine_ranks(e0.elapsed_time(e1), int(np.sum(st_h.numpy() == 0)), dev)
+        e2e_line = {"value": conv_e2e * steps / (ms_e2e / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * B * g.n * 16 + (out_np.nbytes if n1 else 0),
+                    "d2h_bytes_per_step": B * g.n * 16 + B * 4 + B,
+                    "api": ("pf_solve_batch_outages after page-locked host copies of the outage lists and injections"
+                            if n1 else "pf_solve_batch_host (page-locked host buffers, copies overlapped across calls)")}
 
     # ---- roofline of the dominant kernel (dense trailing update) ----
-    w = 8 if args.lu == "fp64" else 4
+    w = 8 if lu == "fp64" else 4
     ndp = info["dense_pad"]
     kb = info["panel"]
-    refactors = int(iters.sum()) * args.steps  # one refactor per Newton update per instance
+    refactors = int(iters.sum()) * rsteps  # one refactor per Newton update per instance
     du = prof["dense_update"]
-    du_flop = dense_update_flop(ndp, kb) * refactors
-    achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
-    peak = fp64_peak if args.lu == "fp64" else fp32_peak
     hbm, hbm_kind = measured_hbm()
-    # algorithmic bytes of the trailing updates: the trailing block read and
-    # written once per panel, plus the two panels, per refactor
-    du_bytes = dense_update_bytes(ndp, kb, w) * refactors
-    # launches that update something: one set per batch refactor (the body
-    # whose check finds no instance active launches gated no-ops)
-    active_launches = len(dense_update_launches(ndp, kb)) * int(iters.max()) * args.steps
-    r2 = [(ndp - k - kb) ** 2 for k in range(0, ndp, kb) if ndp - k - kb > 0]
-    traffic = (DENSE_UPDATE_DRAM_B_PER_R2 * B * sum(r2) / len(r2)
-               if r2 and args.lu == "fp64" and kb == 8 else None)
+    timing = (f"CUDA events around every dense_update launch on its stream, during a second pass of {rsteps} of "
+              f"the {steps} timed steps")
+    if im:
+        du_flop = sum(2 * r * c * d for L in dense_update_launches_im(ndp) for r, c, d in L) * refactors
+        achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
+        roof = {"bound": "alu", "kernel": "dense_update (k_im_gemm, FP32 CTA-tiled product)", "achieved": achieved,
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": (achieved / fp32_peak) if achieved else None,
+                "traffic": None, "peak_kind": "measured FP32 FMA-chain throughput (pf_fma_peak)",
+                "launches": du[0], "ms_total": du[2], "timing": timing,
+                "bytes_per_flop": "trailing block read and written once per outer panel of 128: 8 B per 256 flop"}
+    elif lu == "fp64":
+        du_flop = dense_update_flop(ndp, kb) * refactors
+        achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
+        r2 = [(ndp - k - kb) ** 2 for k in range(0, ndp, kb) if ndp - k - kb > 0]
+        traffic = (DENSE_UPDATE_DRAM_B_PER_R2 * B * sum(r2) / len(r2) if r2 and kb == 8 else None)
+        roof = {"bound": "alu", "kernel": "dense_update", "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": (achieved / fp64_peak) if achieved else None, "traffic": traffic,
+                "peak_kind": "measured FP64 FMA-chain throughput (pf_fma_peak)",
+                "traffic_kind": "ncu DRAM bytes per average active launch, scaled from a batch-640 capture",
+                "launches": du[0], "ms_total": du[2], "timing": timing}
+    else:
+        du_flop = dense_update_flop(ndp, kb) * refactors
+        achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
+        du_bytes = dense_update_bytes(ndp, kb, w) * refactors
+        active_launches = len(dense_update_launches(ndp, kb)) * int(iters.max()) * rsteps
+        gbs = du_bytes / (du[2] / 1e3) / 1e9 if du[2] > 0 else None
+        roof = {"bound": "hbm", "kernel": "dense_update", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                "frac": (gbs / hbm) if gbs else None,
+                "traffic": DENSE_UPDATE_FP32_DRAM_PER_ALG * du_bytes / max(active_launches, 1),
+                "traffic_kind": "ncu DRAM bytes / algorithmic bytes of a batch-640 depth-64 capture, times the "
+                                "algorithmic bytes per launch",
+                "peak_kind": f"{hbm_kind} HBM copy bandwidth", "fp32_tflops": achieved, "fp32_peak_tflops": fp32_peak,
+                "launches": du[0], "ms_total": du[2], "timing": timing}
     # whole-step HBM roofline (metric's second half): algorithmic bytes per
     # instance-iteration = LU written once and read once + voltages, injections,
     # rhs and solution
     nnz_lu = info["nnz_lu"]
     bmin = 2 * w * nnz_lu + 8 * (8 * g.n + 4 * info["m"])
     step_bytes = bmin * int(iters.sum())
-    hbm_pct = 100.0 * (step_bytes * args.steps / (ms_max / 1e3) / 1e9) / hbm
+    hbm_pct = 100.0 * (step_bytes * steps / (ms_max / 1e3) / 1e9) / hbm
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.lu == "fp64" else "f64+f32lu",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if lu == "fp64" else "f64+f32lu",
         "data": "synthetic",
         "config": {"workload": name, "batch_per_gpu": B, "buses": g.n, "branches": g.n_branch,
-                   "unknowns": info["m"], "lu_precision": args.lu, "tol": TOL, "maxit": args.maxit,
-                   "load_scale": g.load_scale, "dense_block": info["dense_dim"], "panel": kb,
+                   "unknowns": info["m"], "lu_precision": lu, "tol": TOL, "maxit": args.maxit,
+                   "load_scale": g.load_scale, "dense_block": info["dense_dim"], "dense_pad": ndp, "panel": kb,
+                   "dense_layout": "instance-major" if im else "interleaved",
                    "parallelism": f"instances split over {world} GPU(s)",
                    "l2": f"working set > L2: LU workspace {nnz_lu * w * B / 1e9:.1f} GB per GPU",
                    "plan_ms": round(plan_ms, 1)},
         "iterations": {"mean": float(iters.mean()), "max": int(iters.max()),
                        "hist": np.bincount(iters).tolist()},
         "converged": conv, "failed": int(np.sum(status == 2)),
-        "roofline": ({"bound": "alu", "kernel": "dense_update", "achieved": achieved, "peak": peak,
-                      "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                      "peak_kind": "measured FP64 FMA-chain throughput (pf_fma_peak)",
-                      "traffic_kind": "ncu DRAM bytes per average active launch, scaled from a batch-640 capture",
-                      "launches": du[0], "ms_total": du[2], "timing": KERNEL_TIMING}
-                     if args.lu == "fp64" else
-                     {"bound": "hbm", "kernel": "dense_update",
-                      "achieved": du_bytes / (du[2] / 1e3) / 1e9 if du[2] > 0 else None, "peak": hbm,
-                      "unit": "GB/s", "frac": (du_bytes / (du[2] / 1e3) / 1e9 / hbm) if du[2] > 0 else None,
-                      "traffic": DENSE_UPDATE_FP32_DRAM_PER_ALG * du_bytes / active_launches,
-                      "traffic_kind": "ncu DRAM bytes / algorithmic bytes of a batch-640 depth-64 capture, times the "
-                                      "algorithmic bytes per launch",
-                      "peak_kind": f"{hbm_kind} HBM copy bandwidth",
-                      "fp32_tflops": achieved, "fp32_peak_tflops": fp32_peak,
-                      "launches": du[0], "ms_total": du[2], "timing": KERNEL_TIMING}),
+        "roofline": roof,
         "hbm_roofline": {"algorithmic_bytes_per_instance_iteration": bmin,
-                         "achieved_gbs": step_bytes * args.steps / (ms_max / 1e3) / 1e9,
+                         "achieved_gbs": step_bytes * steps / (ms_max / 1e3) / 1e9,
                          "peak_gbs": hbm, "peak_kind": hbm_kind, "pct": hbm_pct},
         "kernel_ms": {k: round(v[2], 3) for k, v in prof.items() if v[1] > 0},
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "api": ("pf_solve_batch_outages after page-locked host copies of the outage lists and injections" if n1
-                        else "pf_solve_batch_host (page-locked host buffers, copies overlapped across calls)")},
         "gpu_launches": launches,
     }
+    if e2e_line is not None:
+        line["e2e"] = e2e_line
     if n1:
         line["config"].update({"contingencies": int(B // len(gridgen.N1_LEVELS)),
                                "load_levels": list(gridgen.N1_LEVELS),
                                "case": "every single-branch outage that keeps the grid connected, per-instance "
                                        "admittances built on the device from the base values and the outaged "
                                        "branch (pf_solve_batch_outages), one injection profile per load level"})
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1, ins,
-                                             gpu=(out[0].cpu().numpy(), iters, status))
-        if not n1:
-            line["cpu_batched"] = cpu_batched_sample(pf, g, S_np, V0_np, args.cpu_seconds)
+    if rank == 0 and world == 1:
+        if with_cpu and not args.no_cpu_baseline:
+            # the timed oracle sample is also the oracle comparison
+            cb = oracle_sample(g, S_np, V0_np, args.cpu_seconds, os.cpu_count() or 1, ins, gpu=(Vg, iters, status))
+            line["vs_oracle"] = dict(cb.pop("vs_oracle"), sample=cb["sample"].split(",")[0])
+            line["cpu_baseline"] = cb
+            if not n1 and g.n <= 2000:
+                line["cpu_batched"] = cpu_batched_sample(pf, g, S_np, V0_np, args.cpu_seconds)
+        elif not n1:
+            line["vs_oracle"] = vs_oracle(g, S_np, V0_np, Vg, iters, status, sample_indices(B), args.maxit)
+    plan.close()
+    del S, V0, out
+    torch.cuda.empty_cache()
+    return line
+
+
+def summary(line):
+    """The keys of a workload's line kept when it rides along as an extra."""
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "iterations", "converged", "failed",
+            "roofline", "hbm_roofline", "e2e", "vs_oracle", "cpu_baseline", "cpu_batched", "gpu_launches", "clocks")
+    return {k: line[k] for k in keep if k in line}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2101_02270_gb300 as pf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    big = args.config == "mesh9000_b10k"
+    roof = args.roofline_steps or (4 if big else None)
+    line = measure_mesh(args, pf, args.config, args.lu, args.steps, args.warmup, dev, rank, world, roof_steps=roof)
+    if big and rank == 0 and world == 1 and not args.no_extras:
+        # plain FP64 on the first 320 instances of the same batch: the
+        # iteration and accuracy change of the FP32 LU, and its speed-up
+        sub = measure_mesh(args, pf, "mesh9000_b10k", "fp64", 1, 1, dev, with_cpu=False, batch=320, e2e=False)
+        line["fp64_subset"] = summary(sub)
+        extra_steps, extra_warm = min(args.steps, 10), min(args.warmup, 3)
+        line["extras"] = {
+            "mesh2000_b10k_fp64": summary(measure_mesh(args, pf, "mesh2000_b10k", "fp64", extra_steps, extra_warm, dev)),
+            "mesh2000_b10k_fp32lu": summary(measure_mesh(args, pf, "mesh2000_b10k", "fp32", extra_steps, extra_warm,
+                                                         dev, with_cpu=False)),
+            "warmstart2000": warmstart_measure(args, extra_steps, extra_warm),
+        }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if world > 1:
         dist.destroy_process_group()
 
 
 def main():
     args = parse_args()
-    args.lu_explicit = "--lu" in sys.argv
+    args.lu_explicit = args.lu is not None
+    if args.lu is None:
+        args.lu = "fp32" if args.config == "mesh9000_b10k" else "fp64"
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "feeders256x100":
