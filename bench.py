@@ -75,6 +75,8 @@ def parse_args():
     ap.add_argument("--chunk", type=int, default=0,
                     help="instances per chunk of the end-to-end host solve (0 = about a quarter of the batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the oracle comparison of the GPU results (profiling runs)")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload only: skip the 2,000-bus, warm-start and FP64-subset keys")
     ap.add_argument("--roofline-steps", type=int, default=0,
@@ -350,6 +352,11 @@ def combine_ranks(ms, converged, device):
 # ncu DRAM bytes over algorithmic bytes of the depth-64 FP32 trailing update
 # (371.7 MB of 419.4 MB, profiles/dense_update_fp32_mesh2000.md).
 DENSE_UPDATE_FP32_DRAM_PER_ALG = 371.7 / 419.4
+
+# ncu DRAM bytes (read + write) of one k_im_gemm launch per instance and per
+# element r^2 of its trailing block, from the capture summarised in
+# profiles/im_gemm_mesh9000_b64.md (batch 64, r = 2,048): 2.227 GB.
+IM_GEMM_DRAM_B_PER_R2 = 8.30
 
 KERNEL_TIMING = ("CUDA events around every dense_update launch on its stream, during a second pass of the "
                  "K timed steps")
@@ -895,9 +902,13 @@ def measure_mesh(args, pf, name, lu, steps, warmup, dev, rank=0, world=1, with_c
     if im:
         du_flop = sum(2 * r * c * d for L in dense_update_launches_im(ndp) for r, c, d in L) * refactors
         achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
+        r2 = [r * c for L in dense_update_launches_im(ndp) for r, c, d in L]
         roof = {"bound": "alu", "kernel": "dense_update (k_im_gemm, FP32 CTA-tiled product)", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": (achieved / fp32_peak) if achieved else None,
-                "traffic": None, "peak_kind": "measured FP32 FMA-chain throughput (pf_fma_peak)",
+                "traffic": IM_GEMM_DRAM_B_PER_R2 * B * sum(r2) / len(r2) if r2 else None,
+                "traffic_kind": "ncu DRAM bytes per element of the trailing block of a batch-64 capture, times the "
+                                "batch and the mean r^2 of the refactor's launches",
+                "peak_kind": "measured FP32 FMA-chain throughput (pf_fma_peak)",
                 "launches": du[0], "ms_total": du[2], "timing": timing,
                 "bytes_per_flop": "trailing block read and written once per outer panel of 128: 8 B per 256 flop"}
     elif lu == "fp64":
@@ -970,7 +981,7 @@ def measure_mesh(args, pf, name, lu, steps, warmup, dev, rank=0, world=1, with_c
             line["cpu_baseline"] = cb
             if not n1 and g.n <= 2000:
                 line["cpu_batched"] = cpu_batched_sample(pf, g, S_np, V0_np, args.cpu_seconds)
-        elif not n1:
+        elif not n1 and not args.no_oracle:
             line["vs_oracle"] = vs_oracle(g, S_np, V0_np, Vg, iters, status, sample_indices(B), args.maxit)
     plan.close()
     del S, V0, out

@@ -322,10 +322,14 @@ int pf_stage_linear_solve(pf_plan* p, int B, const double* v, const double* rhs,
  * same LU precision and no dense block, i.e. created with dense_frac >= 1) and
  * different scenario counts are solved together by one persistent kernel
  * (the paper's remark on imbalanced batches across streams/GPUs, Sec. 5,
- * motivates it).  Work items are (plan, tile of up to 32 scenarios), sorted
+ * motivates it).  Work items are (plan, tile of up to S scenarios), sorted
  * by decreasing work and pulled from a device counter; each item runs the
- * full Newton loop of Sec. 3 in a private workspace slot.  The launch is
- * captured in a CUDA graph and replayed while arguments are unchanged. */
+ * full Newton loop of Sec. 3, the S scenarios of the item sharing each warp
+ * (32 / S workers per scenario and warp).  Its state (voltages, injections,
+ * right-hand side, LU values) sits in the CTA's shared memory when it fits
+ * (pf_multi_set_scenarios with use_smem), otherwise in a private global
+ * slot.  The launch is captured in a CUDA graph and replayed while arguments
+ * are unchanged. */
 typedef struct pf_multi pf_multi;
 
 /* host in: k plans (kept alive by the caller while the group exists) and
@@ -346,9 +350,22 @@ int pf_multi_solve(pf_multi* mp, const double* sbus, const double* v0, double to
 int pf_multi_set_config(pf_multi* mp, int warps, int blocks_per_sm);
 int pf_multi_get_config(const pf_multi* mp, int* warps, int* blocks_per_sm, int64_t* instances, int* items);
 
-/* Autotuner: times the real solve for every (warps, CTAs per SM) pair in
- * {1,2,4,8,16}^2 with at most 2048 threads per SM, keeps the fastest and
- * reports its time (host-blocking; outputs hold the last solve). */
+/* Scenarios per work item S (1, 2, 4, ..., 32; default 32) and whether item
+ * states that fit 200 KB go to shared memory (use_smem 1; the launch then
+ * takes the largest such state as its dynamic shared memory per CTA).
+ * Rebuilds the item list; may grow the slot pool (allocation, synchronous).
+ * Errors: NRPF_ERR_ARG (S not a power of two in [1, 32], use_smem not 0/1),
+ * NRPF_ERR_NOMEM, NRPF_ERR_CUDA. */
+int pf_multi_set_scenarios(pf_multi* mp, int per_item, int use_smem);
+/* Current S, use_smem, dynamic shared memory per CTA (bytes) and the number of
+ * items whose state is in shared memory. */
+int pf_multi_get_scenarios(const pf_multi* mp, int* per_item, int* use_smem, int64_t* smem_bytes, int* smem_items);
+
+/* Autotuner: times the real solve for every (S, use_smem) in {(32, 0), (32, 1),
+ * (16, 1), (8, 1), (4, 1), (2, 1)} and (warps, CTAs per SM) pair in
+ * {1,2,4,8,16}^2 with at most 2048 threads and 228 KB of dynamic shared
+ * memory per SM, keeps the fastest and reports its time (host-blocking;
+ * outputs hold the last solve). */
 int pf_multi_autotune(pf_multi* mp, const double* sbus, const double* v0, double tol, int maxit, double* v_out,
                       int32_t* iters, uint8_t* status, void* stream, double* best_ms);
 

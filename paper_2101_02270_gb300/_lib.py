@@ -51,7 +51,7 @@ EXPORTS = ["pf_options_default", "pf_ybus_from_branches", "pf_plan_create", "pf_
            "pf_plan_get_pattern", "pf_solve_batch", "pf_solve_batch_host", "pf_solve_batch_y", "pf_ybus_values", "pf_plan_set_branches", "pf_solve_batch_outages", "pf_branch_flows", "pf_solve_pivoting_host", "pf_retry_failed", "pf_solve_batch_cpu", "pf_stage_mismatch", "pf_stage_factor",
            "pf_stage_linear_solve", "pf_profile_start", "pf_profile_read", "pf_kernel_class_name",
            "pf_fma_peak", "pf_stage_mismatch_noalloc", "pf_multi_create", "pf_multi_solve",
-           "pf_multi_set_config", "pf_multi_get_config", "pf_multi_autotune", "pf_multi_destroy",
+           "pf_multi_set_config", "pf_multi_get_config", "pf_multi_set_scenarios", "pf_multi_get_scenarios", "pf_multi_autotune", "pf_multi_destroy",
            "pf_mlp_create", "pf_mlp_set_norm", "pf_mlp_fit_norm", "pf_mlp_params", "pf_mlp_grads",
            "pf_mlp_predict", "pf_mlp_train_step", "pf_mlp_error", "pf_mlp_destroy", "pf_gemm_bf16",
            "pf_gemm_set_variant",
@@ -94,6 +94,8 @@ def _load():
     lib.pf_multi_set_config.argtypes = [P, I, I]
     lib.pf_multi_get_config.argtypes = [P, C.POINTER(I), C.POINTER(I), C.POINTER(I64), C.POINTER(I)]
     lib.pf_multi_autotune.argtypes = [P, P, P, D, I, P, P, P, P, C.POINTER(D)]
+    lib.pf_multi_set_scenarios.argtypes = [P, I, I]
+    lib.pf_multi_get_scenarios.argtypes = [P, C.POINTER(I), C.POINTER(I), C.POINTER(I64), C.POINTER(I)]
     lib.pf_multi_destroy.argtypes = [P]
     lib.pf_multi_destroy.restype = None
     lib.pf_mlp_create.argtypes = [I, I, I, I, I, C.c_uint64, C.POINTER(C.c_void_p)]

@@ -458,23 +458,13 @@ int pf_plan_create(int n, const int32_t* rowptr, const int32_t* colidx, const do
     return rc;
   }
   {
-    // instance-major dense block: it is zeroed before the Jacobian fill, so
-    // only the Schur tasks with products run (the others would write zeros
-    // and Jacobian entries already in place)
-    std::vector<int32_t> task_list;
-    std::vector<uint32_t> jmask;
-    for (size_t t = 0; t < h.schur_jmask.size(); ++t) {
-      if (d.dim && h.schur_task[4 * t + 2] == h.schur_task[4 * t + 3]) continue;
-      task_list.insert(task_list.end(), h.schur_task.begin() + 4 * t, h.schur_task.begin() + 4 * t + 4);
-      jmask.push_back(h.schur_jmask[t]);
-    }
     const int32_t* tasks = nullptr;
-    if ((rc = upload(p, task_list, &tasks)) || (rc = upload(p, jmask, &d.schur_jmask))) {
+    if ((rc = upload(p, h.schur_task, &tasks)) || (rc = upload(p, h.schur_jmask, &d.schur_jmask))) {
       pf_plan_destroy(p);
       return rc;
     }
     d.schur_task = reinterpret_cast<const int4*>(tasks);
-    d.n_schur = (int)(task_list.size() / 4);
+    d.n_schur = (int)(h.schur_task.size() / 4);
   }
   if (o.max_batch > 0 && (rc = ensure_capacity(p, o.max_batch))) {
     pf_plan_destroy(p);

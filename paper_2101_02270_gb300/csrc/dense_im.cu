@@ -287,9 +287,9 @@ __global__ void __launch_bounds__(kImGemmThreads, 2)
 // L(ki:ki+64, k:k+64) U(k:k+64, ki:ki+64) of the outer panel's first step (a
 // 4 x 4 register tile per thread).  Unblocked right-looking elimination in
 // shared memory: the pivot column is scaled by the reciprocal of the pivot,
-// then the trailing block takes the rank-1 update.  Then 64 threads form
-// U11^-1 column by column (back substitution) and 64 more L11^-1 (forward
-// substitution, unit diagonal); they go to the instance's slot of S.inv as
+// then the trailing block takes the rank-1 update, and the same row
+// operations on an identity block give L11^-1.  A backward sweep over the
+// rows of [U | I] then gives U11^-1.  Both go to the instance's slot of S.inv as
 //   ui[q * 64 + c] = U11^-1(q, c),  li[q * 64 + r] = L11^-1(r, q)
 // (zero outside the triangles), the operands the panel kernel multiplies by.
 // Shared memory (dynamic): D[c][r] = A(ki + r, ki + c), and two work arrays
@@ -351,45 +351,47 @@ __global__ void __launch_bounds__(kImDiagThreads) k_im_diag(DevPlan P, DevState 
       for (int rr = 0; rr < 4; ++rr) D[c4 + cc][r4 + rr] = acc[cc][rr];
     __syncthreads();
   }
+  // LU of D; the same row operations applied to an identity block give
+  // L11^-1 (forward elimination on [D | I]): at step p, row r > p of LI takes
+  // -L(r, p) times row p, whose entries c <= p are final.
+  //   LI[q * kInvPitch + r] = L11^-1(r, q)   (stored by column q)
+  float* UI = &W1[0][0];  // UI[q * kInvPitch + c] = U11^-1(q, c)
+  float* LI = &W2[0][0];
+  for (int e = tid; e < 64 * kInvPitch; e += kImDiagThreads) {
+    const int q = e / kInvPitch, r = e - q * kInvPitch;
+    UI[e] = (q == r) ? 1.f : 0.f;
+    LI[e] = (q == r) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  // thread (tr, tc) = (tid % 64, tid / 64): row tr, every fourth column
+  const int tr = tid & 63, tc = tid >> 6;
   for (int p = 0; p < 64; ++p) {
     const float inv = 1.f / D[p][p];
     if (tid > p && tid < 64) D[p][tid] *= inv;
     __syncthreads();
-    const int n = 63 - p;
-    for (int e = tid; e < n * n; e += kImDiagThreads) {
-      const int r = p + 1 + e % n, c = p + 1 + e / n;
-      D[c][r] = fmaf(-D[p][r], D[c][p], D[c][r]);
+    if (tr > p) {
+      const float l = D[p][tr];
+      for (int c = p + 1 + tc; c < 64; c += 4) D[c][tr] = fmaf(-l, D[c][p], D[c][tr]);
+      // row tr of L^-1, columns q <= p
+      for (int q = tc; q <= p; q += 4) LI[q * kInvPitch + tr] = fmaf(-l, LI[q * kInvPitch + p], LI[q * kInvPitch + tr]);
     }
     __syncthreads();
   }
-  // inverses: zero both arrays (their other triangles stay zero), then a
-  // thread per column
-  float* UI = &W1[0][0];  // UI[q * kInvPitch + c] = U11^-1(q, c)
-  float* LI = &W2[0][0];  // LI[q * kInvPitch + r] = L11^-1(r, q)
-  for (int e = tid; e < 64 * kInvPitch; e += kImDiagThreads) {
-    UI[e] = 0.f;
-    LI[e] = 0.f;
-  }
   if (tid < 64) invd[tid] = 1.f / D[tid][tid];
   __syncthreads();
-  if (tid < 64) {
-    const int c = tid;  // column c of U^-1: z_c = 1/U(c,c), z_r = -(sum_{p=r+1..c} U(r,p) z_p) / U(r,r)
-    UI[c * kInvPitch + c] = invd[c];
-    for (int r = c - 1; r >= 0; --r) {
-      float sum = 0.f;
-      for (int p = r + 1; p <= c; ++p) sum = fmaf(D[p][r], UI[p * kInvPitch + c], sum);
-      UI[r * kInvPitch + c] = -sum * invd[r];
+  // U11^-1 by a backward sweep over the rows of [U | I]: at step p, row p is
+  // final once scaled by 1/U(p,p); rows r < p take -U(r, p) times it.  Each
+  // thread scales its own copy of the row-p entry, so the row is scaled in
+  // place after the barrier.
+  for (int p = 63; p >= 0; --p) {
+    if (tr < p) {
+      const float u = D[p][tr] * invd[p];
+      for (int c = p + tc; c < 64; c += 4) UI[tr * kInvPitch + c] = fmaf(-u, UI[p * kInvPitch + c], UI[tr * kInvPitch + c]);
     }
-  } else if (tid < 128) {
-    const int q = tid - 64;  // column q of L^-1: w_q = 1, w_r = -sum_{p=q..r-1} L(r,p) w_p
-    LI[q * kInvPitch + q] = 1.f;
-    for (int r = q + 1; r < 64; ++r) {
-      float sum = 0.f;
-      for (int p = q; p < r; ++p) sum = fmaf(D[p][r], LI[q * kInvPitch + p], sum);
-      LI[q * kInvPitch + r] = -sum;
-    }
+    __syncthreads();
+    if (tid >= p && tid < 64) UI[p * kInvPitch + tid] *= invd[p];
+    __syncthreads();
   }
-  __syncthreads();
   float* __restrict__ inv_out = reinterpret_cast<float*>(S.inv) + (size_t)b * 8192;
   for (int e = tid; e < 64 * 64; e += kImDiagThreads) {
     const int c = e >> 6, r = e & 63;

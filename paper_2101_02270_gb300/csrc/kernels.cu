@@ -513,16 +513,16 @@ __global__ void __launch_bounds__(32 * kSchurWarps, sizeof(T) == 8 ? 7 : 1) k_sc
       // instance-major block: instance l's 32 rows of column task.x are one
       // contiguous 128-byte line, written by the whole warp (lane = row)
       __syncwarp();
-      // (the block was zeroed and has received the Jacobian entries: the sums
-      // are subtracted in place)
       const int nr = min(32, P.ndp - 32 * task.y);
+      const bool jrow = (jm >> lane) & 1u;
       float* __restrict__ col = LUb + (size_t)P.NS * kTile + (size_t)task.x * P.ndp + 32 * task.y + lane;
       const size_t bstride = (size_t)P.ndp * (size_t)P.ndp;
       if (lane < nr) {
 #pragma unroll 4
         for (int l = 0; l < 32; ++l) {
           float* q = col + (size_t)l * bstride;
-          *q -= a[lane][l];
+          const float sum = a[lane][l];
+          *q = jrow ? *q - sum : -sum;
         }
       }
       return;
@@ -1106,9 +1106,7 @@ void launch_prepare_lu(const DevPlan& P, const DevState& S, const int32_t* gate,
   // (both multiples of 128 bytes).  The dense block is left alone unless
   // `whole`: the Schur tasks then write every position of it.
   const size_t stride16 = (size_t)P.NLU * kTile * sizeof(T) / 16;
-  // (instance-major dense block: zeroed too; its Schur tasks then subtract
-  // their products in place, and the chunks without products are skipped)
-  const size_t n16 = (whole || P.nd == 0 || P.dim) ? stride16 : (size_t)P.NS * kTile * sizeof(T) / 16;
+  const size_t n16 = (whole || P.nd == 0) ? stride16 : (size_t)P.NS * kTile * sizeof(T) / 16;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

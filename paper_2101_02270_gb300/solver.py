@@ -383,8 +383,17 @@ class MultiPlan:
     def set_config(self, warps, blocks_per_sm):
         check(lib.pf_multi_set_config(self._h, int(warps), int(blocks_per_sm)), "pf_multi_set_config")
 
+    def set_scenarios(self, per_item, use_smem=True):
+        """Scenarios per work item (power of two <= 32) and whether item
+        states that fit go to shared memory."""
+        check(lib.pf_multi_set_scenarios(self._h, int(per_item), int(bool(use_smem))), "pf_multi_set_scenarios")
+
     @property
     def config(self):
         w, b, n, i = C.c_int(0), C.c_int(0), C.c_int64(0), C.c_int(0)
         check(lib.pf_multi_get_config(self._h, C.byref(w), C.byref(b), C.byref(n), C.byref(i)), "config")
-        return {"warps": w.value, "blocks_per_sm": b.value, "instances": n.value, "items": i.value}
+        s, u, sb, si = C.c_int(0), C.c_int(0), C.c_int64(0), C.c_int(0)
+        check(lib.pf_multi_get_scenarios(self._h, C.byref(s), C.byref(u), C.byref(sb), C.byref(si)), "scenarios")
+        return {"warps": w.value, "blocks_per_sm": b.value, "instances": n.value, "items": i.value,
+                "scenarios_per_item": s.value, "shared_memory": bool(u.value), "smem_bytes": sb.value,
+                "smem_items": si.value}

@@ -75,6 +75,30 @@ def test_multi_feeders_uneven(lu, exact):
     mp.close()
 
 
+@pytest.mark.parametrize("lu,exact", [("fp64", True), ("fp32", False)])
+@pytest.mark.parametrize("per_item,smem", [(32, True), (8, True), (4, True), (1, True), (8, False)])
+def test_multi_scenarios_per_item_and_shared_memory(lu, exact, per_item, smem):
+    """Items of S scenarios (lanes split into S scenarios x 32/S workers),
+    state in shared memory where it fits: every instance equals the oracle's
+    (ragged tiles: batches not multiples of S)."""
+    fs, scen = _feeders([(13,), (3,), (21,), (1,), (9,)])
+    plans, mp, S, V0, Sc, Vc = _group(fs, scen, lu)
+    mp.set_scenarios(per_item, smem)
+    cfg = mp.config
+    assert cfg["scenarios_per_item"] == per_item and cfg["shared_memory"] == smem
+    assert cfg["items"] == sum(-(-s.shape[0] // per_item) for s in S)
+    assert cfg["smem_bytes"] <= 200 * 1024 and (cfg["smem_items"] > 0) == (cfg["smem_bytes"] > 0)
+    if not smem:
+        assert cfg["smem_items"] == 0
+    elif per_item <= 4:  # a few scenarios of a feeder fit in 200 KB
+        assert cfg["smem_items"] > 0
+    for w, b in [(1, 2), (4, 1)]:
+        mp.set_config(w, b)
+        v, it, st = mp.solve(Sc, Vc, TOL, 10)
+        _check(fs, S, V0, v, it, st, exact)
+    mp.close()
+
+
 def test_multi_meshed_and_feeders_mixed():
     """A meshed 30-bus grid and two feeders in one group."""
     g, S0, V00 = case("mesh30_b64", batch=40)
@@ -91,7 +115,7 @@ def test_multi_autotune_and_graph_replay():
     fs, scen = _feeders([(40,), (9,), (70,)])
     plans, mp, S, V0, Sc, Vc = _group(fs, scen, "fp32")
     cfg = mp.autotune(Sc, Vc, TOL, 10)
-    assert cfg["ms"] > 0 and 1 <= cfg["warps"] <= 16
+    assert cfg["ms"] > 0 and 1 <= cfg["warps"] <= 16 and cfg["scenarios_per_item"] in (1, 2, 4, 8, 16, 32)
     out = mp._outs(Sc)
     a = mp.solve(Sc, Vc, TOL, 10, out=out)
     a = [t.clone() for t in a]
