@@ -361,8 +361,8 @@ int pf_multi_set_scenarios(pf_multi* mp, int per_item, int use_smem);
  * items whose state is in shared memory. */
 int pf_multi_get_scenarios(const pf_multi* mp, int* per_item, int* use_smem, int64_t* smem_bytes, int* smem_items);
 
-/* Autotuner: times the real solve for every (S, use_smem) in {(32, 0), (32, 1),
- * (16, 1), (8, 1), (4, 1), (2, 1)} and (warps, CTAs per SM) pair in
+/* Autotuner: times the real solve for every (S, use_smem) in {(32, 0), (16, 0),
+ * (8, 0), (32, 1), (16, 1), (8, 1), (4, 1), (2, 1)} and (warps, CTAs per SM) pair in
  * {1,2,4,8,16}^2 with at most 2048 threads and 228 KB of dynamic shared
  * memory per SM, keeps the fastest and reports its time (host-blocking;
  * outputs hold the last solve). */

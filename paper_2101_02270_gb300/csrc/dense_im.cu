@@ -43,7 +43,16 @@ constexpr int kImTile = 128;                // GEMM tile (rows and columns of C)
 constexpr int kImKc = 32;                   // GEMM depth per stage
 constexpr int kImChunks = kImOuter / kImKc;
 constexpr int kImStages = 2;
-constexpr int kImGemmThreads = 256;
+// column groups of 32 per thread in the trailing update: 2 (an 8 x 8 register
+// tile, 8 warps per CTA) or 4 (8 x 16, 4 warps).  The wider tile needs fewer
+// shared-memory wavefronts per FMA but leaves half the warps; measured on the
+// 9,000-bus trailing update it is 1 % slower, so the 8 x 8 tile is used.
+constexpr int kImGC = 2;
+// packed two-wide FP32 FMA (fma.rn.f32x2) in the trailing update: each
+// instruction updates two rows of a column; the B chunk is negated while it is
+// transposed, so acc + a (-b) rounds exactly as fmaf(-a, b, acc)
+constexpr bool kImPacked = false;
+constexpr int kImGemmThreads = 32 * 4 * (4 / kImGC);
 constexpr uint32_t kImABytes = kImKc * kImTile * 4;  // 16 KB: [32 columns][128 rows]
 constexpr uint32_t kImBBytes = kImTile * kImKc * 4;  // 16 KB: [128 columns][32 rows], swizzled
 constexpr uint32_t kImStageBytes = kImABytes + kImBBytes;
@@ -110,10 +119,10 @@ __device__ __forceinline__ float comp(const float4& v, int q) {
 // then every thread runs the register-tiled product: per kk two 16-byte loads
 // of A and two of B feed 64 FMAs, the next kk's fragments loaded while the
 // current ones are used.
-// Warp w = (wy, wx), wy = w % 4, wx = w / 4, owns the 32 x 64 block at rows
-// 32 wy, columns 64 wx of the tile; its lane (lx, ly), lx = lane % 8,
-// ly = lane / 8, owns rows 32 wy + ly*4 + 16h + q and columns 64 wx + lx*4 +
-// 32g + r (h, g < 2; q, r < 4).  Every shared load of a warp then touches four
+// Warp w = (wy, wx), wy = w % 4, wx = w / 4, owns the 32 x (32 kImGC) block at
+// rows 32 wy, columns 32 kImGC wx of the tile; its lane (lx, ly), lx = lane % 8,
+// ly = lane / 8, owns rows 32 wy + ly*4 + 16h + q and columns 32 kImGC wx +
+// lx*4 + 32g + r (h < 2, g < kImGC; q, r < 4).  Every shared load of a warp then touches four
 // (A) or eight (B) distinct 16-byte words of one 128-byte row: one wavefront.
 // A tile whose rows (columns) run past ndp has 64 of them; the warps outside
 // skip the arithmetic (the TMA box past ndp is filled with zeros, unused).
@@ -135,11 +144,12 @@ __device__ __forceinline__ void issue_chunk(uint8_t* sm, uint64_t* full, const C
   tma_4d(sa + kImABytes, tmB, k + kc * kImKc, j0, lane_b, tile_b, &full[s]);
 }
 
-__device__ __forceinline__ void fma_kk(float (&acc)[2][2][4][4], const float4 (&a)[2], const float4 (&b)[2]) {
+__device__ __forceinline__ void fma_kk(float (&acc)[2][kImGC][4][4], const float4 (&a)[2],
+                                       const float4 (&b)[kImGC]) {
 #pragma unroll
   for (int h = 0; h < 2; ++h)
 #pragma unroll
-    for (int g = 0; g < 2; ++g)
+    for (int g = 0; g < kImGC; ++g)
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const float bv = comp(b[g], r);
@@ -151,25 +161,51 @@ __device__ __forceinline__ void fma_kk(float (&acc)[2][2][4][4], const float4 (&
       }
 }
 
+// the same update on packed pairs: acc2[h][g][r][p] = rows 2p, 2p+1 of the
+// thread's 4-row group h, column g, r; b holds -B
+__device__ __forceinline__ void fma_kk2(float2 (&acc)[2][kImGC][4][2], const float4 (&a)[2],
+                                        const float4 (&b)[kImGC]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float2 a01 = make_float2(a[h].x, a[h].y), a23 = make_float2(a[h].z, a[h].w);
+#pragma unroll
+    for (int g = 0; g < kImGC; ++g)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float bv = comp(b[g], r);
+        const float2 b2 = make_float2(bv, bv);
+        acc[h][g][r][0] = __ffma2_rn(a01, b2, acc[h][g][r][0]);
+        acc[h][g][r][1] = __ffma2_rn(a23, b2, acc[h][g][r][1]);
+      }
+  }
+}
+
 __device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, int j0, int k, uint8_t* sm,
                                          uint64_t* full, const CUtensorMap* tmA, const CUtensorMap* tmB, int lane_b,
                                          int tile_b, bool active, int rw, int cw, int lx, int ly) {
-  // acc[h][g][r][q]: row rw + ly*4 + 16h + q, column cw + lx*4 + 32g + r
-  float acc[2][2][4][4];
+  // acc[h][g][r][q] (acc2: the same as pairs of q): row rw + ly*4 + 16h + q,
+  // column cw + lx*4 + 32g + r
+  float acc[2][kImGC][4][4];
+  float2 acc2[2][kImGC][4][2];
   const size_t cstride = (size_t)ld;
   if (active) {
     const float* __restrict__ Ct = C + (size_t)(j0 + cw + lx * 4) * ld + i0 + rw + ly * 4;
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int g = 0; g < 2; ++g)
+      for (int g = 0; g < kImGC; ++g)
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const float4 v = *reinterpret_cast<const float4*>(Ct + (size_t)(32 * g + r) * cstride + 16 * h);
-          acc[h][g][r][0] = v.x;
-          acc[h][g][r][1] = v.y;
-          acc[h][g][r][2] = v.z;
-          acc[h][g][r][3] = v.w;
+          if constexpr (kImPacked) {
+            acc2[h][g][r][0] = make_float2(v.x, v.y);
+            acc2[h][g][r][1] = make_float2(v.z, v.w);
+          } else {
+            acc[h][g][r][0] = v.x;
+            acc[h][g][r][1] = v.y;
+            acc[h][g][r][2] = v.z;
+            acc[h][g][r][3] = v.w;
+          }
         }
   }
   float* Bt0 = reinterpret_cast<float*>(sm + (size_t)kImStages * kImStageBytes);
@@ -187,10 +223,11 @@ __device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, 
 #pragma unroll
       for (int q = tid >> 7; q < kImKc / 4; q += kImGemmThreads / kImTile) {
         const float4 v = *reinterpret_cast<const float4*>(Bs + j * 128 + ((q ^ (j & 7)) << 4));
-        Bt[(4 * q) * kImTile + j] = v.x;
-        Bt[(4 * q + 1) * kImTile + j] = v.y;
-        Bt[(4 * q + 2) * kImTile + j] = v.z;
-        Bt[(4 * q + 3) * kImTile + j] = v.w;
+        const float sg = kImPacked ? -1.f : 1.f;
+        Bt[(4 * q) * kImTile + j] = sg * v.x;
+        Bt[(4 * q + 1) * kImTile + j] = sg * v.y;
+        Bt[(4 * q + 2) * kImTile + j] = sg * v.z;
+        Bt[(4 * q + 3) * kImTile + j] = sg * v.w;
       }
     }
     // one barrier: the chunk has landed for everyone, Bt is complete, and
@@ -201,25 +238,27 @@ __device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, 
     if (active) {
       const float* As = reinterpret_cast<const float*>(sm + (size_t)s * kImStageBytes) + rw + ly * 4;
       const float* Bq = Bt + cw + lx * 4;
-      float4 a[2], b[2];
+      float4 a[2], b[kImGC];
       a[0] = *reinterpret_cast<const float4*>(As);
       a[1] = *reinterpret_cast<const float4*>(As + 16);
-      b[0] = *reinterpret_cast<const float4*>(Bq);
-      b[1] = *reinterpret_cast<const float4*>(Bq + 32);
+#pragma unroll
+      for (int g = 0; g < kImGC; ++g) b[g] = *reinterpret_cast<const float4*>(Bq + 32 * g);
 #pragma unroll 8
       for (int kk = 0; kk < kImKc - 1; ++kk) {
-        float4 an[2], bn[2];
+        float4 an[2], bn[kImGC];
         an[0] = *reinterpret_cast<const float4*>(As + (kk + 1) * kImTile);
         an[1] = *reinterpret_cast<const float4*>(As + (kk + 1) * kImTile + 16);
-        bn[0] = *reinterpret_cast<const float4*>(Bq + (kk + 1) * kImTile);
-        bn[1] = *reinterpret_cast<const float4*>(Bq + (kk + 1) * kImTile + 32);
-        fma_kk(acc, a, b);
+#pragma unroll
+        for (int g = 0; g < kImGC; ++g) bn[g] = *reinterpret_cast<const float4*>(Bq + (kk + 1) * kImTile + 32 * g);
+        if constexpr (kImPacked) fma_kk2(acc2, a, b);
+        else fma_kk(acc, a, b);
         a[0] = an[0];
         a[1] = an[1];
-        b[0] = bn[0];
-        b[1] = bn[1];
+#pragma unroll
+        for (int g = 0; g < kImGC; ++g) b[g] = bn[g];
       }
-      fma_kk(acc, a, b);
+      if constexpr (kImPacked) fma_kk2(acc2, a, b);
+      else fma_kk(acc, a, b);
     }
   }
   if (active) {
@@ -227,11 +266,12 @@ __device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, 
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int g = 0; g < 2; ++g)
+      for (int g = 0; g < kImGC; ++g)
 #pragma unroll
         for (int r = 0; r < 4; ++r)
           *reinterpret_cast<float4*>(Ct + (size_t)(32 * g + r) * cstride + 16 * h) =
-              make_float4(acc[h][g][r][0], acc[h][g][r][1], acc[h][g][r][2], acc[h][g][r][3]);
+              kImPacked ? make_float4(acc2[h][g][r][0].x, acc2[h][g][r][0].y, acc2[h][g][r][1].x, acc2[h][g][r][1].y)
+                        : make_float4(acc[h][g][r][0], acc[h][g][r][1], acc[h][g][r][2], acc[h][g][r][3]);
   }
   return -1;
 }
@@ -255,7 +295,7 @@ __global__ void __launch_bounds__(kImGemmThreads, 2)
   // shared array keeps the pointer in the shared address space)
   uint8_t* sm = im_smem_raw + ((1024u - (su32(im_smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int rw = (warp & 3) * 32, cw = (warp >> 2) * 64;
+  const int rw = (warp & 3) * 32, cw = (warp >> 2) * 32 * kImGC;
   const int lane_b = b & 31, tile_b = b >> 5;
   if (tid == 0) {
     for (int s = 0; s < kImStages; ++s) bar_init(&full[s], 1);
@@ -418,7 +458,8 @@ __global__ void __launch_bounds__(kImDiagThreads) k_im_diag(DevPlan P, DevState 
 // stops at q < 32 (wn + 1).
 // ---------------------------------------------------------------------------
 constexpr int kImPanelThreads2 = 256;
-constexpr size_t kImPanelSmemPre = (size_t)(64 * 128 + 64 * 64 + 64 * 128 + 64 * 64) * sizeof(float);
+// Pk (reused for T2 once the left-looking product is done), Qk, Q2
+constexpr size_t kImPanelSmemPre = (size_t)(64 * 128 + 64 * 64 + 64 * 64) * sizeof(float);
 constexpr size_t kImPanelSmem = (size_t)(64 * 128 + 64 * 64) * sizeof(float);
 
 __device__ __forceinline__ void fma_q(float (&acc)[2][4][4], const float4 (&a)[2], const float4& b, float sign) {
@@ -436,13 +477,13 @@ __device__ __forceinline__ void fma_q(float (&acc)[2][4][4], const float4 (&a)[2
 }
 
 template <bool PRE>
-__global__ void __launch_bounds__(kImPanelThreads2, 2) k_im_panel(DevPlan P, DevState S, int k, int ki, int nch,
+__global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, DevState S, int k, int ki, int nch,
                                                                const int32_t* __restrict__ gate) {
   extern __shared__ __align__(16) float pan_smem[];
   float* Pk = pan_smem;                           // PRE: [64 q][128 m]
-  float* Qk = pan_smem + 64 * 128;                // PRE: [64 q][64 n]
-  float* T2 = pan_smem + (PRE ? 64 * 128 + 64 * 64 : 0);  // [64 n][128 m]: the first result, k-major
-  float* Q2 = T2 + 64 * 128;                      // [64 q][64 n]: the inverse factor
+  float* T2 = pan_smem;                           // [64 n][128 m]: the first result, k-major (over Pk)
+  float* Q2 = pan_smem + 64 * 128;                // [64 q][64 n]: the inverse factor
+  float* Qk = Q2 + 64 * 64;                       // PRE: [64 q][64 n]
   if (gate && *gate == 0) return;
   const int per = 2 * nch;
   const int b = (int)(blockIdx.x / (unsigned)per);
@@ -534,6 +575,7 @@ __global__ void __launch_bounds__(kImPanelThreads2, 2) k_im_panel(DevPlan P, Dev
       fma_q(acc, a, bq, -1.f);
     }
   }
+  if (PRE) __syncthreads();  // T2 overwrites Pk
   if (active) {
 #pragma unroll
     for (int h = 0; h < 2; ++h)

@@ -584,9 +584,9 @@ int pf_multi_autotune(pf_multi* mp, const double* sbus, const double* v0, double
   int bw = mp->warps, bb = mp->blocks_per_sm, bs = mp->scen, bm = mp->use_smem;
   const int warps_c[] = {1, 2, 4, 8, 16};
   const int bps_c[] = {1, 2, 4, 8, 16};
-  // scenarios per item with the state in global slots (32) or, where it
-  // fits, in shared memory (32 .. 2)
-  const int scen_c[][2] = {{32, 0}, {32, 1}, {16, 1}, {8, 1}, {4, 1}, {2, 1}};
+  // scenarios per item with the state in global slots (32, 16, 8) or, where
+  // it fits, in shared memory (32 .. 2)
+  const int scen_c[][2] = {{32, 0}, {16, 0}, {8, 0}, {32, 1}, {16, 1}, {8, 1}, {4, 1}, {2, 1}};
   int rc = NRPF_OK;
   for (const auto& sc : scen_c) {
     if ((rc = pf_multi_set_scenarios(mp, sc[0], sc[1]))) break;
