@@ -24,7 +24,7 @@
 //                        depth 128: one 128 x 128 tile of C per CTA, operand
 //                        chunks of depth 32 loaded by TMA into a two-stage
 //                        shared-memory ring, an 8 x 8 register tile per thread
-//                        on the FP32 FMA pipe.
+//                        updated with packed two-wide FP32 FMAs.
 // The trailing update takes the subtractions into each entry in ascending
 // pivot order, as the interleaved kernels do.  The panel multiplies by the
 // explicit inverses of the 64 x 64 diagonal factors (the LU is the FP32 inner
@@ -51,7 +51,7 @@ constexpr int kImGC = 2;
 // packed two-wide FP32 FMA (fma.rn.f32x2) in the trailing update: each
 // instruction updates two rows of a column; the B chunk is negated while it is
 // transposed, so acc + a (-b) rounds exactly as fmaf(-a, b, acc)
-constexpr bool kImPacked = false;
+constexpr bool kImPacked = true;
 constexpr int kImGemmThreads = 32 * 4 * (4 / kImGC);
 constexpr uint32_t kImABytes = kImKc * kImTile * 4;  // 16 KB: [32 columns][128 rows]
 constexpr uint32_t kImBBytes = kImTile * kImKc * 4;  // 16 KB: [128 columns][32 rows], swizzled
