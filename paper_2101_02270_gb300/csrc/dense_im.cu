@@ -462,18 +462,24 @@ constexpr int kImPanelThreads2 = 256;
 constexpr size_t kImPanelSmemPre = (size_t)(64 * 128 + 64 * 64 + 64 * 64) * sizeof(float);
 constexpr size_t kImPanelSmem = (size_t)(64 * 128 + 64 * 64) * sizeof(float);
 
-__device__ __forceinline__ void fma_q(float (&acc)[2][4][4], const float4 (&a)[2], const float4& b, float sign) {
+// acc[h][r][p] holds rows (2p, 2p+1) of the thread's 4-row group h, column
+// r; one packed two-wide FMA per pair (same rounding as fmaf)
+__device__ __forceinline__ void fma_q(float2 (&acc)[2][4][2], const float4 (&a)[2], const float4& b, float sign) {
 #pragma unroll
-  for (int h = 0; h < 2; ++h)
+  for (int h = 0; h < 2; ++h) {
+    const float2 a01 = make_float2(a[h].x, a[h].y), a23 = make_float2(a[h].z, a[h].w);
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const float bv = sign * comp(b, r);
-      float* d = acc[h][r];
-      d[0] = fmaf(a[h].x, bv, d[0]);
-      d[1] = fmaf(a[h].y, bv, d[1]);
-      d[2] = fmaf(a[h].z, bv, d[2]);
-      d[3] = fmaf(a[h].w, bv, d[3]);
+      const float2 b2 = make_float2(bv, bv);
+      acc[h][r][0] = __ffma2_rn(a01, b2, acc[h][r][0]);
+      acc[h][r][1] = __ffma2_rn(a23, b2, acc[h][r][1]);
     }
+  }
+}
+
+__device__ __forceinline__ float& el(float2 (&acc)[2][4][2], int h, int r, int q) {
+  return (q & 1) ? acc[h][r][q >> 1].y : acc[h][r][q >> 1].x;
 }
 
 template <bool PRE>
@@ -538,8 +544,8 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
       }
     }
   }
-  // acc[h][r][q] = T(m = mo + 16h + q, n = no + r)
-  float acc[2][4][4];
+  // el(acc, h, r, q) = T(m = mo + 16h + q, n = no + r); pairs of q packed
+  float2 acc[2][4][2];
   if (active) {
     if (rows) {
 #pragma unroll
@@ -547,10 +553,8 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const float4 v = *reinterpret_cast<const float4*>(A + (size_t)(ki + no + r) * ld + base + mo + 16 * h);
-          acc[h][r][0] = v.x;
-          acc[h][r][1] = v.y;
-          acc[h][r][2] = v.z;
-          acc[h][r][3] = v.w;
+          acc[h][r][0] = make_float2(v.x, v.y);
+          acc[h][r][1] = make_float2(v.z, v.w);
         }
     } else {
 #pragma unroll
@@ -558,10 +562,10 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const float4 v = *reinterpret_cast<const float4*>(A + (size_t)(base + mo + 16 * h + q) * ld + ki + no);
-          acc[h][0][q] = v.x;
-          acc[h][1][q] = v.y;
-          acc[h][2][q] = v.z;
-          acc[h][3][q] = v.w;
+          el(acc, h, 0, q) = v.x;
+          el(acc, h, 1, q) = v.y;
+          el(acc, h, 2, q) = v.z;
+          el(acc, h, 3, q) = v.w;
         }
     }
   }
@@ -582,16 +586,17 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
 #pragma unroll
       for (int r = 0; r < 4; ++r)
         *reinterpret_cast<float4*>(T2 + (no + r) * 128 + mo + 16 * h) =
-            make_float4(acc[h][r][0], acc[h][r][1], acc[h][r][2], acc[h][r][3]);
+            make_float4(acc[h][r][0].x, acc[h][r][0].y, acc[h][r][1].x, acc[h][r][1].y);
   }
   __syncthreads();
   if (!active) return;
 #pragma unroll
   for (int h = 0; h < 2; ++h)
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[h][r][q] = 0.f;
+    for (int r = 0; r < 4; ++r) {
+      acc[h][r][0] = make_float2(0.f, 0.f);
+      acc[h][r][1] = make_float2(0.f, 0.f);
+    }
   const int qend = 32 * (wn + 1);
 #pragma unroll 4
   for (int q = 0; q < qend; ++q) {
@@ -606,14 +611,14 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
 #pragma unroll
       for (int r = 0; r < 4; ++r)
         *reinterpret_cast<float4*>(A + (size_t)(ki + no + r) * ld + base + mo + 16 * h) =
-            make_float4(acc[h][r][0], acc[h][r][1], acc[h][r][2], acc[h][r][3]);
+            make_float4(acc[h][r][0].x, acc[h][r][0].y, acc[h][r][1].x, acc[h][r][1].y);
   } else {
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         *reinterpret_cast<float4*>(A + (size_t)(base + mo + 16 * h + q) * ld + ki + no) =
-            make_float4(acc[h][0][q], acc[h][1][q], acc[h][2][q], acc[h][3][q]);
+            make_float4(el(acc, h, 0, q), el(acc, h, 1, q), el(acc, h, 2, q), el(acc, h, 3, q));
   }
 }
 
