@@ -757,11 +757,23 @@ def sample_indices(B, k=8, seed=0):
 
 
 def dense_update_launches_im(ndp):
-    """The k_im_gemm launches of one instance-major dense refactor: per outer
-    panel of 128 at column k, the trailing block [k+128, ndp)^2 with depth
-    128 (the second 64-wide step's left-looking products are counted with the
+    """The k_im_gemm launches of one instance-major dense refactor, each a list
+    of (rows, columns, depth) pieces.  Per pair of outer panels of 128 at
+    columns k, k2 = k+128: the second panel's block column and row with depth
+    128 (rows [k2, ndp) x columns [k2, k2+c) and rows [k2, k2+c) x columns
+    [k2+128, ndp), c = min(128, ndp-k2)), then [k+256, ndp)^2 with depth 256
+    (the second 64-wide step's left-looking products are counted with the
     diagonal and panel kernels)."""
-    return [[(ndp - k - 128, ndp - k - 128, 128)] for k in range(0, ndp, 128) if ndp - k - 128 > 0]
+    out = []
+    for k in range(0, ndp, 256):
+        k2 = k + 128
+        if k2 >= ndp:
+            break
+        c = min(128, ndp - k2)
+        out.append([(ndp - k2, c, 128), (c, max(0, ndp - k2 - 128), 128)])
+        if ndp - k - 256 > 0:
+            out.append([(ndp - k - 256, ndp - k - 256, 256)])
+    return out
 
 
 def measure_mesh(args, pf, name, lu, steps, warmup, dev, rank=0, world=1, with_cpu=True, batch=None,
@@ -902,7 +914,7 @@ def measure_mesh(args, pf, name, lu, steps, warmup, dev, rank=0, world=1, with_c
     if im:
         du_flop = sum(2 * r * c * d for L in dense_update_launches_im(ndp) for r, c, d in L) * refactors
         achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
-        r2 = [r * c for L in dense_update_launches_im(ndp) for r, c, d in L]
+        r2 = [sum(r * c for r, c, d in L) for L in dense_update_launches_im(ndp)]
         roof = {"bound": "alu", "kernel": "dense_update (k_im_gemm, FP32 CTA-tiled product)", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": (achieved / fp32_peak) if achieved else None,
                 "traffic": IM_GEMM_DRAM_B_PER_R2 * B * sum(r2) / len(r2) if r2 else None,
@@ -910,7 +922,8 @@ def measure_mesh(args, pf, name, lu, steps, warmup, dev, rank=0, world=1, with_c
                                 "batch and the mean r^2 of the refactor's launches",
                 "peak_kind": "measured FP32 FMA-chain throughput (pf_fma_peak)",
                 "launches": du[0], "ms_total": du[2], "timing": timing,
-                "bytes_per_flop": "trailing block read and written once per outer panel of 128: 8 B per 256 flop"}
+                "bytes_per_flop": "C read and written once per launch: 8 B per 512 flop in the depth-256 "
+                                  "launches, per 256 flop in the depth-128 block row and column updates"}
     elif lu == "fp64":
         du_flop = dense_update_flop(ndp, kb) * refactors
         achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None

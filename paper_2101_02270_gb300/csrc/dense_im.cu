@@ -20,11 +20,15 @@
 //   k_im_panel (step 1): rows below / columns right of k+128, each first minus
 //                        its product with step 0's L or U (left-looking within
 //                        the outer panel), then multiplied by the inverse;
-//   k_im_gemm          : A22 -= L21 U12 over rows/columns [k+128, ndp) with
-//                        depth 128: one 128 x 128 tile of C per CTA, operand
-//                        chunks of depth 32 loaded by TMA into a two-stage
-//                        shared-memory ring, an 8 x 8 register tile per thread
-//                        updated with packed two-wide FP32 FMAs.
+//   k_im_gemm          : A22 -= L21 U12: one 128 x 128 tile of C per CTA,
+//                        operand chunks of depth 32 loaded by TMA into a
+//                        two-stage shared-memory ring, an 8 x 8 register tile
+//                        per thread updated with packed two-wide FP32 FMAs.
+// Outer panels go in pairs (k, k+128).  After the first, k_im_gemm updates
+// only the second's block column and row (rows and columns [k+128, k+256),
+// depth 128); after the second, the rest of the trailing block, [k+256, ndp)^2,
+// takes both panels' products in one pass of depth 256, which halves the
+// reads and writes of C per multiply-add.
 // The trailing update takes the subtractions into each entry in ascending
 // pivot order, as the interleaved kernels do.  The panel multiplies by the
 // explicit inverses of the 64 x 64 diagonal factors (the LU is the FP32 inner
@@ -180,7 +184,7 @@ __device__ __forceinline__ void fma_kk2(float2 (&acc)[2][kImGC][4][2], const flo
   }
 }
 
-__device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, int j0, int k, uint8_t* sm,
+__device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, int j0, int k, int nkc, uint8_t* sm,
                                          uint64_t* full, const CUtensorMap* tmA, const CUtensorMap* tmB, int lane_b,
                                          int tile_b, bool active, int rw, int cw, int lx, int ly) {
   // acc[h][g][r][q] (acc2: the same as pairs of q): row rw + ly*4 + 16h + q,
@@ -211,7 +215,7 @@ __device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, 
   float* Bt0 = reinterpret_cast<float*>(sm + (size_t)kImStages * kImStageBytes);
   const int tid = threadIdx.x;
 #pragma unroll 1
-  for (int kc = 0; kc < kImChunks; ++kc) {
+  for (int kc = 0; kc < nkc; ++kc) {
     const int s = kc % kImStages;
     const bool ok = bar_wait(&full[s], (uint32_t)(kc / kImStages) & 1u);
     // transpose the B chunk: thread tid takes column j = tid % 128 and the
@@ -233,7 +237,7 @@ __device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, 
     // one barrier: the chunk has landed for everyone, Bt is complete, and
     // every warp is done with chunk kc - 1 (its stage may be refilled)
     if (__syncthreads_or(!ok)) return kc;
-    if (kc >= 1 && kc + 1 < kImChunks && tid == 0)
+    if (kc >= 1 && kc + 1 < nkc && tid == 0)
       issue_chunk(sm, full, tmA, tmB, kc + 1, i0, j0, k, lane_b, tile_b);
     if (active) {
       const float* As = reinterpret_cast<const float*>(sm + (size_t)s * kImStageBytes) + rw + ly * 4;
@@ -276,21 +280,34 @@ __device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, 
   return -1;
 }
 
-// grid: Bp * ntc^2 CTAs, tile-fastest within an instance, so that the CTAs
-// resident at one time share their instance's L21 and U12 panels in L2.
+// C region from row and column r0 on, in tiles of 128: all ntc^2 tiles of
+// [r0, ld)^2, or (lshape) its first tile column and first tile row, 2 ntc - 1
+// tiles; depth nkc chunks of 32 from pivot column k.  grid: Bp * (tiles) CTAs,
+// tile-fastest within an instance, so that the CTAs resident at one time
+// share their instance's L21 and U12 panels in L2.
 __global__ void __launch_bounds__(kImGemmThreads, 2)
     k_im_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, DevPlan P,
-              DevState S, int k, int ntc, const int32_t* __restrict__ gate) {
+              DevState S, int k, int nkc, int r0, int ntc, int lshape, const int32_t* __restrict__ gate) {
   extern __shared__ uint8_t im_smem_raw[];
   __shared__ __align__(8) uint64_t full[kImStages];
   if (gate && *gate == 0) return;
-  const int ntile = ntc * ntc;
+  const int ntile = lshape ? 2 * ntc - 1 : ntc * ntc;
   const int b = (int)(blockIdx.x / (unsigned)ntile);
   const int t = (int)(blockIdx.x - (unsigned)b * (unsigned)ntile);
   if (!S.active[b]) return;
   const int ld = P.ndp;
-  const int r0 = k + kImOuter;
-  const int i0 = r0 + (t % ntc) * kImTile, j0 = r0 + (t / ntc) * kImTile;
+  int ti, tj;
+  if (!lshape) {
+    ti = t % ntc;
+    tj = t / ntc;
+  } else if (t < ntc) {
+    ti = t;
+    tj = 0;
+  } else {
+    ti = 0;
+    tj = t - ntc + 1;
+  }
+  const int i0 = r0 + ti * kImTile, j0 = r0 + tj * kImTile;
   // 1024-byte alignment for the swizzled B chunks (offset arithmetic on the
   // shared array keeps the pointer in the shared address space)
   uint8_t* sm = im_smem_raw + ((1024u - (su32(im_smem_raw) & 1023u)) & 1023u);
@@ -303,20 +320,20 @@ __global__ void __launch_bounds__(kImGemmThreads, 2)
   }
   __syncthreads();
   if (tid == 0)
-    for (int kc = 0; kc < kImStages && kc < kImChunks; ++kc)
+    for (int kc = 0; kc < kImStages && kc < nkc; ++kc)
       issue_chunk(sm, full, &tmA, &tmB, kc, i0, j0, k, lane_b, tile_b);
   // rows (columns) of this tile inside the block: 128, or 64 at the edge
   const int mrows = ld - i0 < kImTile ? ld - i0 : kImTile;
   const int ncols = ld - j0 < kImTile ? ld - j0 : kImTile;
   const bool active = rw < mrows && cw < ncols;
-  const int fail = gemm_tile(im_block(P, S, b), ld, i0, j0, k, sm, full, &tmA, &tmB, lane_b, tile_b, active, rw, cw,
+  const int fail = gemm_tile(im_block(P, S, b), ld, i0, j0, k, nkc, sm, full, &tmA, &tmB, lane_b, tile_b, active, rw, cw,
                              lane & 7, lane >> 3);
   if (fail >= 0 && tid == 0) {
     // a copy did not land in time: the instance is marked failed (its step
     // is discarded) and the CTA waits, bounded, for the copies it issued
     // (chunks up to fail + 1: one chunk ahead of the one consumed)
     S.bad[b] = 1;
-    const int issued = fail + 2 < kImChunks ? fail + 2 : kImChunks;
+    const int issued = fail + 2 < nkc ? fail + 2 : nkc;
     for (int kc = fail; kc < issued; ++kc) bar_wait(&full[kc % kImStages], (uint32_t)(kc / kImStages) & 1u);
   }
 }
@@ -777,7 +794,8 @@ void launch_dense_im_factor(const DevPlan& P, const DevState& S, const DenseImMa
   }
   const unsigned Bp = (unsigned)S.Bp;
   const int ld = P.ndp;
-  for (int k = 0; k < ld; k += kImOuter) {
+  // the two 64-wide steps of the outer panel at k
+  auto outer = [&](int k) {
     NRPF_LAUNCH(rec, K_DENSE_DIAG, st,
                 k_im_diag<false><<<Bp, kImDiagThreads, kImDiagSmem, st>>>(P, S, k, k, gate));
     int nr = ld - k - 64;
@@ -786,7 +804,7 @@ void launch_dense_im_factor(const DevPlan& P, const DevState& S, const DenseImMa
       NRPF_LAUNCH(rec, K_DENSE_PANEL, st,
                   k_im_panel<false><<<Bp * 2 * nch, kImPanelThreads2, kImPanelSmem, st>>>(P, S, k, k, nch, gate));
     }
-    if (ld - k < kImOuter) break;  // a last outer panel of 64
+    if (ld - k < kImOuter) return;  // a last outer panel of 64
     NRPF_LAUNCH(rec, K_DENSE_DIAG, st,
                 k_im_diag<true><<<Bp, kImDiagThreads, kImDiagSmem, st>>>(P, S, k, k + 64, gate));
     nr = ld - k - kImOuter;
@@ -795,11 +813,29 @@ void launch_dense_im_factor(const DevPlan& P, const DevState& S, const DenseImMa
       NRPF_LAUNCH(rec, K_DENSE_PANEL, st,
                   k_im_panel<true><<<Bp * 2 * nch, kImPanelThreads2, kImPanelSmemPre, st>>>(P, S, k, k + 64, nch,
                                                                                           gate));
-      const int ntc = (nr + kImTile - 1) / kImTile;
-      NRPF_LAUNCH(rec, K_DENSE_UPDATE, st,
-                  k_im_gemm<<<Bp * (unsigned)(ntc * ntc), kImGemmThreads, kImGemmSmem, st>>>(maps.a, maps.b, P, S,
-                                                                                           k, ntc, gate));
     }
+  };
+  // C from row and column r0 on minus the products over pivot columns
+  // k .. k + 32 nkc - 1
+  auto gemm = [&](int k, int nkc, int r0, int lshape) {
+    const int ntc = (ld - r0 + kImTile - 1) / kImTile;
+    if (ntc <= 0) return;
+    const unsigned ntile = lshape ? (unsigned)(2 * ntc - 1) : (unsigned)(ntc * ntc);
+    NRPF_LAUNCH(rec, K_DENSE_UPDATE, st,
+                k_im_gemm<<<Bp * ntile, kImGemmThreads, kImGemmSmem, st>>>(maps.a, maps.b, P, S, k, nkc, r0, ntc,
+                                                                         lshape, gate));
+  };
+  // Outer panels in pairs (k, k + 128): after the first, only the second's
+  // block column and row take its update (depth 128); after the second, the
+  // rest of the trailing block takes both at once (depth 256), each entry's
+  // subtractions still in ascending pivot order.
+  for (int k = 0; k < ld; k += 2 * kImOuter) {
+    outer(k);
+    const int k2 = k + kImOuter;
+    if (k2 >= ld) break;
+    gemm(k, kImChunks, k2, 1);
+    outer(k2);
+    if (k2 + kImOuter < ld) gemm(k, 2 * kImChunks, k2 + kImOuter, 0);
   }
 }
 

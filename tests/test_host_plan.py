@@ -273,8 +273,8 @@ def test_dense_layout_selection_and_validation():
 
 def test_instance_major_update_accounting_matches_lu_arithmetic():
     """bench.py's flop count of the instance-major trailing updates (k_im_gemm:
-    per outer panel of 128, the block right of and below it with depth 128)
-    plus the work of the diagonal and panel kernels (64-wide steps, the second
+    per pair of outer panels of 128, the second one's block column and row
+    with depth 128, then the rest of the trailing block with depth 256) plus the work of the diagonal and panel kernels (64-wide steps, the second
     step of an outer panel first taking its left-looking product with the
     first) equals the multiply-adds of a right-looking LU without pivoting."""
     import importlib.util
