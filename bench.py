@@ -353,10 +353,11 @@ def combine_ranks(ms, converged, device):
 # (371.7 MB of 419.4 MB, profiles/dense_update_fp32_mesh2000.md).
 DENSE_UPDATE_FP32_DRAM_PER_ALG = 371.7 / 419.4
 
-# ncu DRAM bytes (read + write) of one k_im_gemm launch per instance and per
-# element r^2 of its trailing block, from the capture summarised in
-# profiles/im_gemm_mesh9000_b64.md (batch 64, r = 2,048): 2.227 GB.
-IM_GEMM_DRAM_B_PER_R2 = 8.30
+# ncu DRAM bytes (read + write) of one k_im_gemm launch over its algorithmic
+# bytes (im_update_bytes), from the capture summarised in
+# profiles/im_gemm_mesh9000_b64.md (batch 64, outer panel 8: 739.5 MB
+# against 746.6 MB).
+IM_GEMM_DRAM_PER_ALG = 0.99
 
 KERNEL_TIMING = ("CUDA events around every dense_update launch on its stream, during a second pass of the "
                  "K timed steps")
@@ -758,22 +759,25 @@ def sample_indices(B, k=8, seed=0):
 
 def dense_update_launches_im(ndp):
     """The k_im_gemm launches of one instance-major dense refactor, each a list
-    of (rows, columns, depth) pieces.  Per pair of outer panels of 128 at
-    columns k, k2 = k+128: the second panel's block column and row with depth
-    128 (rows [k2, ndp) x columns [k2, k2+c) and rows [k2, k2+c) x columns
-    [k2+128, ndp), c = min(128, ndp-k2)), then [k+256, ndp)^2 with depth 256
-    (the second 64-wide step's left-looking products are counted with the
-    diagonal and panel kernels)."""
+    of (rows, columns, depth) pieces.  Left-looking by outer panels of 128:
+    before panel j (at kj = 128 j, j > 0) is factorised, its block column and
+    row take depth kj (rows [kj, ndp) x columns [kj, kj+c) and rows [kj, kj+c)
+    x columns [kj+128, ndp), c = min(128, ndp-kj)) (the second 64-wide step's
+    left-looking products are counted with the diagonal and panel kernels)."""
     out = []
-    for k in range(0, ndp, 256):
-        k2 = k + 128
-        if k2 >= ndp:
-            break
-        c = min(128, ndp - k2)
-        out.append([(ndp - k2, c, 128), (c, max(0, ndp - k2 - 128), 128)])
-        if ndp - k - 256 > 0:
-            out.append([(ndp - k - 256, ndp - k - 256, 256)])
+    for kj in range(128, ndp, 128):
+        c = min(128, ndp - kj)
+        out.append([(ndp - kj, c, kj), (c, max(0, ndp - kj - 128), kj)])
     return out
+
+
+def im_update_bytes(ndp, kj):
+    """Algorithmic bytes of the k_im_gemm launch of outer panel kj, per
+    instance: its block column and row read and written once (8 B per entry)
+    and the operands L(kj:, :kj) and U(:kj, kj:) read once (4 B each)."""
+    c = min(128, ndp - kj)
+    entries = (ndp - kj) * c + c * max(0, ndp - kj - 128)
+    return 8 * entries + 8 * kj * (ndp - kj)
 
 
 def measure_mesh(args, pf, name, lu, steps, warmup, dev, rank=0, world=1, with_cpu=True, batch=None,
@@ -914,16 +918,17 @@ def measure_mesh(args, pf, name, lu, steps, warmup, dev, rank=0, world=1, with_c
     if im:
         du_flop = sum(2 * r * c * d for L in dense_update_launches_im(ndp) for r, c, d in L) * refactors
         achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None
-        r2 = [sum(r * c for r, c, d in L) for L in dense_update_launches_im(ndp)]
+        alg = [im_update_bytes(ndp, kj) for kj in range(128, ndp, 128)]
         roof = {"bound": "alu", "kernel": "dense_update (k_im_gemm, FP32 CTA-tiled product)", "achieved": achieved,
                 "peak": fp32_peak, "unit": "TFLOP/s", "frac": (achieved / fp32_peak) if achieved else None,
-                "traffic": IM_GEMM_DRAM_B_PER_R2 * B * sum(r2) / len(r2) if r2 else None,
-                "traffic_kind": "ncu DRAM bytes per element of the trailing block of a batch-64 capture, times the "
-                                "batch and the mean r^2 of the refactor's launches",
+                "traffic": (IM_GEMM_DRAM_PER_ALG * B * sum(alg) / len(alg)
+                            if alg and IM_GEMM_DRAM_PER_ALG is not None else None),
+                "traffic_kind": "ncu DRAM bytes over algorithmic bytes of one launch of a batch-64 capture, times "
+                                "the batch and the mean algorithmic bytes of the refactor's launches",
                 "peak_kind": "measured FP32 FMA-chain throughput (pf_fma_peak)",
                 "launches": du[0], "ms_total": du[2], "timing": timing,
-                "bytes_per_flop": "C read and written once per launch: 8 B per 512 flop in the depth-256 "
-                                  "launches, per 256 flop in the depth-128 block row and column updates"}
+                "algorithmic_bytes": "per launch and instance: the panel's block column and row read and "
+                                     "written once, the operands L(kj:, :kj) and U(:kj, kj:) read once"}
     elif lu == "fp64":
         du_flop = dense_update_flop(ndp, kb) * refactors
         achieved = du_flop / (du[2] / 1e3) / 1e12 if du[2] > 0 else None

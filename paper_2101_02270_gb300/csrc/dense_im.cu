@@ -7,32 +7,35 @@
 // dense block is its own column-major ndp x ndp matrix,
 //   element (r, c) at lu + ((b / 32) * NLU + NS) * 32 + (b % 32) * ndp^2 + c * ndp + r,
 // inside the same per-tile LU array (only the order of the dense part
-// changes; ndp is a multiple of 64).  The factorisation is right-looking and
-// blocked, without pivoting.  Outer panel k of width 128 (64 for the last one
-// when ndp % 128 == 64):
-//   k_im_diag  (step 0): LU of the 64 x 64 diagonal block at (k, k), and the
+// changes; ndp is a multiple of 64).  The factorisation is blocked, without
+// pivoting, and left-looking by outer panels (blocked Crout).  Outer panel j
+// at column kj = 128 j, of width 128 (64 for the last one when ndp % 128 ==
+// 64):
+//   k_im_gemm          : (j > 0) its block column and row, rows [kj, ndp) x
+//                        columns [kj, kj+128) and rows [kj, kj+128) x columns
+//                        [kj+128, ndp), minus the products of all earlier
+//                        panels in one pass of depth kj: one 128 x 128 tile
+//                        of C per CTA, operand chunks of depth 32 loaded by
+//                        TMA into a two-stage shared-memory ring, an 8 x 8
+//                        register tile per thread updated with packed
+//                        two-wide FP32 FMAs;
+//   k_im_diag  (step 0): LU of the 64 x 64 diagonal block at (kj, kj), and the
 //                        inverses U11^-1, L11^-1 of its factors;
 //   k_im_panel (step 0): L21 = A21 U11^-1 for the rows below and
 //                        U12 = L11^-1 A12 for the columns to the right, as
 //                        register-tiled products on 128 x 64 tiles;
-//   k_im_diag  (step 1): block (k+64, k+64) minus L(., k:k+64) U(k:k+64, .),
+//   k_im_diag  (step 1): block (kj+64, kj+64) minus L(., kj:kj+64) U(kj:kj+64, .),
 //                        then its LU and inverses;
-//   k_im_panel (step 1): rows below / columns right of k+128, each first minus
-//                        its product with step 0's L or U (left-looking within
-//                        the outer panel), then multiplied by the inverse;
-//   k_im_gemm          : A22 -= L21 U12: one 128 x 128 tile of C per CTA,
-//                        operand chunks of depth 32 loaded by TMA into a
-//                        two-stage shared-memory ring, an 8 x 8 register tile
-//                        per thread updated with packed two-wide FP32 FMAs.
-// Outer panels go in pairs (k, k+128).  After the first, k_im_gemm updates
-// only the second's block column and row (rows and columns [k+128, k+256),
-// depth 128); after the second, the rest of the trailing block, [k+256, ndp)^2,
-// takes both panels' products in one pass of depth 256, which halves the
-// reads and writes of C per multiply-add.
-// The trailing update takes the subtractions into each entry in ascending
-// pivot order, as the interleaved kernels do.  The panel multiplies by the
-// explicit inverses of the 64 x 64 diagonal factors (the LU is the FP32 inner
-// solve of an inexact Newton step whose mismatch and update stay FP64).
+//   k_im_panel (step 1): rows below / columns right of kj+128, each first minus
+//                        its product with step 0's L or U, then multiplied by
+//                        the inverse.
+// Every entry of the block is read and written by k_im_gemm once per
+// refactorisation (a right-looking order would rewrite the trailing block
+// after every outer panel), and each entry still takes its subtractions in
+// ascending pivot order, as the interleaved kernels do.  The panel multiplies
+// by the explicit inverses of the 64 x 64 diagonal factors (the LU is the
+// FP32 inner solve of an inexact Newton step whose mismatch and update stay
+// FP64).
 #include <cfloat>
 #include <cstdint>
 
@@ -42,10 +45,9 @@ namespace nrpf {
 
 namespace {
 
-constexpr int kImOuter = 128;               // outer panel width = GEMM depth
+constexpr int kImOuter = 128;               // outer panel width
 constexpr int kImTile = 128;                // GEMM tile (rows and columns of C)
 constexpr int kImKc = 32;                   // GEMM depth per stage
-constexpr int kImChunks = kImOuter / kImKc;
 constexpr int kImStages = 2;
 // column groups of 32 per thread in the trailing update: 2 (an 8 x 8 register
 // tile, 8 warps per CTA) or 4 (8 x 16, 4 warps).  The wider tile needs fewer
@@ -132,7 +134,6 @@ __device__ __forceinline__ float comp(const float4& v, int q) {
 // skip the arithmetic (the TMA box past ndp is filled with zeros, unused).
 // Returns the chunk whose wait ran out, or -1.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kImBtBytes = kImKc * kImTile * 4;  // 16 KB: transposed B chunk [32][128]
 
 // TMA copies of GEMM chunk kc (A: 128 rows x 32 columns, B: 32 rows x 128
 // columns of instance (tile_b, lane_b)) into stage kc % kImStages
@@ -280,34 +281,25 @@ __device__ __forceinline__ int gemm_tile(float* __restrict__ C, int ld, int i0, 
   return -1;
 }
 
-// C region from row and column r0 on, in tiles of 128: all ntc^2 tiles of
-// [r0, ld)^2, or (lshape) its first tile column and first tile row, 2 ntc - 1
-// tiles; depth nkc chunks of 32 from pivot column k.  grid: Bp * (tiles) CTAs,
-// tile-fastest within an instance, so that the CTAs resident at one time
-// share their instance's L21 and U12 panels in L2.
+// The block column and row of the outer panel at r0: tiles of 128 over rows
+// [r0, ld) x columns [r0, r0+128) and rows [r0, r0+128) x columns [r0+128,
+// ld), 2 ntc - 1 of them (ntc = tiles across [r0, ld)), each minus the
+// products over pivot columns 0 .. r0-1 (r0 / 32 chunks).  grid: Bp * (2 ntc
+// - 1) CTAs, tile-fastest within an instance, so that the CTAs resident at
+// one time share their instance's operand panels in L2.
 __global__ void __launch_bounds__(kImGemmThreads, 2)
     k_im_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, DevPlan P,
-              DevState S, int k, int nkc, int r0, int ntc, int lshape, const int32_t* __restrict__ gate) {
+              DevState S, int r0, int ntc, const int32_t* __restrict__ gate) {
   extern __shared__ uint8_t im_smem_raw[];
   __shared__ __align__(8) uint64_t full[kImStages];
   if (gate && *gate == 0) return;
-  const int ntile = lshape ? 2 * ntc - 1 : ntc * ntc;
+  const int ntile = 2 * ntc - 1;
   const int b = (int)(blockIdx.x / (unsigned)ntile);
   const int t = (int)(blockIdx.x - (unsigned)b * (unsigned)ntile);
   if (!S.active[b]) return;
   const int ld = P.ndp;
-  int ti, tj;
-  if (!lshape) {
-    ti = t % ntc;
-    tj = t / ntc;
-  } else if (t < ntc) {
-    ti = t;
-    tj = 0;
-  } else {
-    ti = 0;
-    tj = t - ntc + 1;
-  }
-  const int i0 = r0 + ti * kImTile, j0 = r0 + tj * kImTile;
+  const int k = 0, nkc = r0 / kImKc;
+  const int i0 = r0 + (t < ntc ? t : 0) * kImTile, j0 = r0 + (t < ntc ? 0 : t - ntc + 1) * kImTile;
   // 1024-byte alignment for the swizzled B chunks (offset arithmetic on the
   // shared array keeps the pointer in the shared address space)
   uint8_t* sm = im_smem_raw + ((1024u - (su32(im_smem_raw) & 1023u)) & 1023u);
@@ -645,9 +637,12 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
 // columns: the 64 x 64 triangle is copied to shared memory and solved by one
 // warp (two rows per lane, the solved entry broadcast by a shuffle); then every
 // thread updates its rows below (above) the block with the block's 64
-// entries, reading the matrix columns contiguously across the CTA.
+// entries, reading the matrix columns contiguously across the CTA.  The solve
+// reads each instance's block once and is bound by how many loads are in
+// flight: at most 40 registers per thread let six CTAs (six instances) run on
+// an SM instead of four, which halved its time on the 9,000-bus block.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kImSolveThreads) k_im_dsolve(DevPlan P, DevState S,
+__global__ void __launch_bounds__(kImSolveThreads, 6) k_im_dsolve(DevPlan P, DevState S,
                                                               const int32_t* __restrict__ gate) {
   extern __shared__ float xs[];                  // [ndp]
   __shared__ float T[64][65];                    // T[c][r]
@@ -667,7 +662,7 @@ __global__ void __launch_bounds__(kImSolveThreads) k_im_dsolve(DevPlan P, DevSta
     __syncthreads();
     if (warp == 0) {
       float v0 = xs[kb + lane], v1 = xs[kb + 32 + lane];
-#pragma unroll
+#pragma unroll 8
       for (int c = 0; c < 64; ++c) {
         const float xc = __shfl_sync(0xffffffffu, c < 32 ? v0 : v1, c & 31);
         if (lane > c) v0 = fmaf(-T[c][lane], xc, v0);
@@ -679,7 +674,7 @@ __global__ void __launch_bounds__(kImSolveThreads) k_im_dsolve(DevPlan P, DevSta
     __syncthreads();
     for (int r = kb + 64 + tid; r < ld; r += kImSolveThreads) {
       float acc = xs[r];
-#pragma unroll 16
+#pragma unroll 8
       for (int c = 0; c < 64; ++c) acc = fmaf(-A[(size_t)(kb + c) * ld + r], xs[kb + c], acc);
       xs[r] = acc;
     }
@@ -693,7 +688,7 @@ __global__ void __launch_bounds__(kImSolveThreads) k_im_dsolve(DevPlan P, DevSta
     __syncthreads();
     if (warp == 0) {
       float v0 = xs[kb + lane], v1 = xs[kb + 32 + lane];
-#pragma unroll
+#pragma unroll 8
       for (int c = 63; c >= 0; --c) {
         if (c >= 32) {
           if (lane == c - 32) v1 = v1 * (1.f / T[c][c]);
@@ -710,7 +705,7 @@ __global__ void __launch_bounds__(kImSolveThreads) k_im_dsolve(DevPlan P, DevSta
     __syncthreads();
     for (int r = tid; r < kb; r += kImSolveThreads) {
       float acc = xs[r];
-#pragma unroll 16
+#pragma unroll 8
       for (int c = 0; c < 64; ++c) acc = fmaf(-A[(size_t)(kb + c) * ld + r], xs[kb + c], acc);
       xs[r] = acc;
     }
@@ -815,27 +810,20 @@ void launch_dense_im_factor(const DevPlan& P, const DevState& S, const DenseImMa
                                                                                           gate));
     }
   };
-  // C from row and column r0 on minus the products over pivot columns
-  // k .. k + 32 nkc - 1
-  auto gemm = [&](int k, int nkc, int r0, int lshape) {
+  // block column and row of the outer panel at r0 minus the products of the
+  // panels before it
+  auto gemm = [&](int r0) {
     const int ntc = (ld - r0 + kImTile - 1) / kImTile;
-    if (ntc <= 0) return;
-    const unsigned ntile = lshape ? (unsigned)(2 * ntc - 1) : (unsigned)(ntc * ntc);
     NRPF_LAUNCH(rec, K_DENSE_UPDATE, st,
-                k_im_gemm<<<Bp * ntile, kImGemmThreads, kImGemmSmem, st>>>(maps.a, maps.b, P, S, k, nkc, r0, ntc,
-                                                                         lshape, gate));
+                k_im_gemm<<<Bp * (unsigned)(2 * ntc - 1), kImGemmThreads, kImGemmSmem, st>>>(maps.a, maps.b, P, S,
+                                                                                            r0, ntc, gate));
   };
-  // Outer panels in pairs (k, k + 128): after the first, only the second's
-  // block column and row take its update (depth 128); after the second, the
-  // rest of the trailing block takes both at once (depth 256), each entry's
-  // subtractions still in ascending pivot order.
-  for (int k = 0; k < ld; k += 2 * kImOuter) {
-    outer(k);
-    const int k2 = k + kImOuter;
-    if (k2 >= ld) break;
-    gemm(k, kImChunks, k2, 1);
-    outer(k2);
-    if (k2 + kImOuter < ld) gemm(k, 2 * kImChunks, k2 + kImOuter, 0);
+  // Left-looking by outer panels: panel j's block column and row first take
+  // the products of panels 0 .. j-1 (depth kj, each entry's subtractions in
+  // ascending pivot order, as in the right-looking form), then it is factorised.
+  for (int kj = 0; kj < ld; kj += kImOuter) {
+    if (kj > 0) gemm(kj);
+    outer(kj);
   }
 }
 

@@ -26,10 +26,10 @@ struct DenseImMaps {
 // encoder is unavailable or rejects the shape.
 bool make_dense_im_maps(const DevPlan& P, void* lu, int Bp, DenseImMaps* out);
 
-// Right-looking blocked LU without pivoting of every active instance's dense
-// block (outer panels of 128 factorised in two 64-wide steps; per pair of
-// outer panels, the second one's block row and column updated with depth 128
-// before it is factorised, then the rest of the trailing block with depth 256).
+// Blocked LU without pivoting of every active instance's dense block, left-
+// looking by outer panels of 128: each panel's block column and row first
+// take the products of all earlier panels (one update of depth 128 j for
+// panel j), then the panel is factorised in two 64-wide steps.
 void launch_dense_im_factor(const DevPlan& P, const DevState& S, const DenseImMaps& maps, const int32_t* gate,
                             cudaStream_t st, Recorder* rec);
 

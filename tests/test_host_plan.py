@@ -272,11 +272,11 @@ def test_dense_layout_selection_and_validation():
 
 
 def test_instance_major_update_accounting_matches_lu_arithmetic():
-    """bench.py's flop count of the instance-major trailing updates (k_im_gemm:
-    per pair of outer panels of 128, the second one's block column and row
-    with depth 128, then the rest of the trailing block with depth 256) plus the work of the diagonal and panel kernels (64-wide steps, the second
-    step of an outer panel first taking its left-looking product with the
-    first) equals the multiply-adds of a right-looking LU without pivoting."""
+    """bench.py's flop count of the instance-major block updates (k_im_gemm,
+    left-looking: each outer panel's block column and row with all earlier
+    panels) plus the work of the diagonal and panel kernels (64-wide steps, the second step of an outer panel first taking its
+    left-looking product with the first) equals the multiply-adds of a
+    right-looking LU without pivoting."""
     import importlib.util
     import pathlib
     spec = importlib.util.spec_from_file_location("bench", pathlib.Path(__file__).parent.parent / "bench.py")
