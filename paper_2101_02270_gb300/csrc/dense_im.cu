@@ -460,35 +460,39 @@ __global__ void __launch_bounds__(kImDiagThreads) k_im_diag(DevPlan P, DevState 
 //   columns: T(m, n) = A(ki + n, j),  U12(., j) = L11^-1 [T - L(ki:ki+64, k:k+64) U(k:k+64, j)]
 // (the bracketed product only with PRE, the second step of an outer panel).
 // All operands sit in shared memory k-major: P[q][m], Q[q][n].  Warp w =
-// (wm, wn), wm = w % 4, wn = w / 4, owns m in [32 wm, 32 wm + 32) and n in
-// [32 wn, 32 wn + 32); lane (lx, ly) owns m = 32 wm + ly*4 + 16h + q and
-// n = 32 wn + lx*4 + r (h < 2, q, r < 4): per q two 16-byte loads of P and
-// one of Q feed 32 FMAs.  The inverse is triangular, so the second product
-// stops at q < 32 (wn + 1).
+// (wm, wn), wm = w % 2, wn = w / 2, owns m in [64 wm, 64 wm + 64) and n in
+// [32 wn, 32 wn + 32); lane (lx, ly), lx = lane % 4, ly = lane / 4, owns m =
+// 64 wm + ly*4 + 32h + q and n = 32 wn + lx*4 + 16g + r (h, g < 2; q, r < 4):
+// per q two 16-byte loads of P and two of Q feed 64 FMAs (packed in pairs of
+// m).  The inverse is triangular, so the second product stops at q < 32 (wn +
+// 1).
 // ---------------------------------------------------------------------------
-constexpr int kImPanelThreads2 = 256;
+constexpr int kImPanelThreads2 = 128;
 // Pk (reused for T2 once the left-looking product is done), Qk, Q2
 constexpr size_t kImPanelSmemPre = (size_t)(64 * 128 + 64 * 64 + 64 * 64) * sizeof(float);
 constexpr size_t kImPanelSmem = (size_t)(64 * 128 + 64 * 64) * sizeof(float);
 
-// acc[h][r][p] holds rows (2p, 2p+1) of the thread's 4-row group h, column
-// r; one packed two-wide FMA per pair (same rounding as fmaf)
-__device__ __forceinline__ void fma_q(float2 (&acc)[2][4][2], const float4 (&a)[2], const float4& b, float sign) {
+// acc[h][g][r][p] holds rows (2p, 2p+1) of the thread's 4-row group h,
+// column (g, r); one packed two-wide FMA per pair (same rounding as fmaf)
+__device__ __forceinline__ void fma_q(float2 (&acc)[2][2][4][2], const float4 (&a)[2], const float4 (&b)[2],
+                                      float sign) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const float2 a01 = make_float2(a[h].x, a[h].y), a23 = make_float2(a[h].z, a[h].w);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const float bv = sign * comp(b, r);
-      const float2 b2 = make_float2(bv, bv);
-      acc[h][r][0] = __ffma2_rn(a01, b2, acc[h][r][0]);
-      acc[h][r][1] = __ffma2_rn(a23, b2, acc[h][r][1]);
-    }
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float bv = sign * comp(b[g], r);
+        const float2 b2 = make_float2(bv, bv);
+        acc[h][g][r][0] = __ffma2_rn(a01, b2, acc[h][g][r][0]);
+        acc[h][g][r][1] = __ffma2_rn(a23, b2, acc[h][g][r][1]);
+      }
   }
 }
 
-__device__ __forceinline__ float& el(float2 (&acc)[2][4][2], int h, int r, int q) {
-  return (q & 1) ? acc[h][r][q >> 1].y : acc[h][r][q >> 1].x;
+__device__ __forceinline__ float& el(float2 (&acc)[2][2][4][2], int h, int g, int r, int q) {
+  return (q & 1) ? acc[h][g][r][q >> 1].y : acc[h][g][r][q >> 1].x;
 }
 
 template <bool PRE>
@@ -505,13 +509,13 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
   const int task = (int)(blockIdx.x - (unsigned)b * (unsigned)per);
   if (!S.active[b]) return;
   const int ld = P.ndp, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp & 3, wn = warp >> 2, lx = lane & 7, ly = lane >> 3;
-  const int mo = wm * 32 + ly * 4, no = wn * 32 + lx * 4;
+  const int wm = warp & 1, wn = warp >> 1, lx = lane & 3, ly = lane >> 2;
+  const int mo = wm * 64 + ly * 4, no = wn * 32 + lx * 4;
   float* __restrict__ A = im_block(P, S, b);
   const bool rows = task < nch;
   const int base = ki + 64 + (rows ? task : task - nch) * 128;  // first row (rows) or column (columns)
   const int mvalid = min(128, ld - base);
-  const bool active = wm * 32 < mvalid;
+  const bool active = wm * 64 < mvalid;
   {
     const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(S.inv) + (size_t)b * 8192 +
                                                         (rows ? 0 : 4096));
@@ -553,29 +557,35 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
       }
     }
   }
-  // el(acc, h, r, q) = T(m = mo + 16h + q, n = no + r); pairs of q packed
-  float2 acc[2][4][2];
+  // el(acc, h, g, r, q) = T(m = mo + 32h + q, n = no + 16g + r); pairs of q packed
+  float2 acc[2][2][4][2];
   if (active) {
     if (rows) {
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const float4 v = *reinterpret_cast<const float4*>(A + (size_t)(ki + no + r) * ld + base + mo + 16 * h);
-          acc[h][r][0] = make_float2(v.x, v.y);
-          acc[h][r][1] = make_float2(v.z, v.w);
-        }
+        for (int g = 0; g < 2; ++g)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const float4 v =
+                *reinterpret_cast<const float4*>(A + (size_t)(ki + no + 16 * g + r) * ld + base + mo + 32 * h);
+            acc[h][g][r][0] = make_float2(v.x, v.y);
+            acc[h][g][r][1] = make_float2(v.z, v.w);
+          }
     } else {
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 v = *reinterpret_cast<const float4*>(A + (size_t)(base + mo + 16 * h + q) * ld + ki + no);
-          el(acc, h, 0, q) = v.x;
-          el(acc, h, 1, q) = v.y;
-          el(acc, h, 2, q) = v.z;
-          el(acc, h, 3, q) = v.w;
-        }
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int g = 0; g < 2; ++g) {
+            const float4 v =
+                *reinterpret_cast<const float4*>(A + (size_t)(base + mo + 32 * h + q) * ld + ki + no + 16 * g);
+            el(acc, h, g, 0, q) = v.x;
+            el(acc, h, g, 1, q) = v.y;
+            el(acc, h, g, 2, q) = v.z;
+            el(acc, h, g, 3, q) = v.w;
+          }
     }
   }
   __syncthreads();
@@ -583,8 +593,9 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
 #pragma unroll 4
     for (int q = 0; q < 64; ++q) {
       const float4 a[2] = {*reinterpret_cast<const float4*>(Pk + q * 128 + mo),
-                           *reinterpret_cast<const float4*>(Pk + q * 128 + mo + 16)};
-      const float4 bq = *reinterpret_cast<const float4*>(Qk + q * 64 + no);
+                           *reinterpret_cast<const float4*>(Pk + q * 128 + mo + 32)};
+      const float4 bq[2] = {*reinterpret_cast<const float4*>(Qk + q * 64 + no),
+                            *reinterpret_cast<const float4*>(Qk + q * 64 + no + 16)};
       fma_q(acc, a, bq, -1.f);
     }
   }
@@ -593,41 +604,50 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
-        *reinterpret_cast<float4*>(T2 + (no + r) * 128 + mo + 16 * h) =
-            make_float4(acc[h][r][0].x, acc[h][r][0].y, acc[h][r][1].x, acc[h][r][1].y);
+      for (int g = 0; g < 2; ++g)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          *reinterpret_cast<float4*>(T2 + (no + 16 * g + r) * 128 + mo + 32 * h) =
+              make_float4(acc[h][g][r][0].x, acc[h][g][r][0].y, acc[h][g][r][1].x, acc[h][g][r][1].y);
   }
   __syncthreads();
   if (!active) return;
 #pragma unroll
   for (int h = 0; h < 2; ++h)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      acc[h][r][0] = make_float2(0.f, 0.f);
-      acc[h][r][1] = make_float2(0.f, 0.f);
-    }
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        acc[h][g][r][0] = make_float2(0.f, 0.f);
+        acc[h][g][r][1] = make_float2(0.f, 0.f);
+      }
   const int qend = 32 * (wn + 1);
 #pragma unroll 4
   for (int q = 0; q < qend; ++q) {
     const float4 a[2] = {*reinterpret_cast<const float4*>(T2 + q * 128 + mo),
-                         *reinterpret_cast<const float4*>(T2 + q * 128 + mo + 16)};
-    const float4 bq = *reinterpret_cast<const float4*>(Q2 + q * 64 + no);
+                         *reinterpret_cast<const float4*>(T2 + q * 128 + mo + 32)};
+    const float4 bq[2] = {*reinterpret_cast<const float4*>(Q2 + q * 64 + no),
+                          *reinterpret_cast<const float4*>(Q2 + q * 64 + no + 16)};
     fma_q(acc, a, bq, 1.f);
   }
   if (rows) {
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
-        *reinterpret_cast<float4*>(A + (size_t)(ki + no + r) * ld + base + mo + 16 * h) =
-            make_float4(acc[h][r][0].x, acc[h][r][0].y, acc[h][r][1].x, acc[h][r][1].y);
+      for (int g = 0; g < 2; ++g)
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          *reinterpret_cast<float4*>(A + (size_t)(ki + no + 16 * g + r) * ld + base + mo + 32 * h) =
+              make_float4(acc[h][g][r][0].x, acc[h][g][r][0].y, acc[h][g][r][1].x, acc[h][g][r][1].y);
   } else {
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<float4*>(A + (size_t)(base + mo + 16 * h + q) * ld + ki + no) =
-            make_float4(el(acc, h, 0, q), el(acc, h, 1, q), el(acc, h, 2, q), el(acc, h, 3, q));
+#pragma unroll
+        for (int g = 0; g < 2; ++g)
+          *reinterpret_cast<float4*>(A + (size_t)(base + mo + 32 * h + q) * ld + ki + no + 16 * g) =
+              make_float4(el(acc, h, g, 0, q), el(acc, h, g, 1, q), el(acc, h, g, 2, q), el(acc, h, g, 3, q));
   }
 }
 
