@@ -333,121 +333,123 @@ __global__ void __launch_bounds__(kImGemmThreads, 2)
 // ---------------------------------------------------------------------------
 // LU of the 64 x 64 diagonal block at (ki, ki), one CTA per instance, and the
 // inverses of its factors.  With PRE, the block first receives the product
-// L(ki:ki+64, k:k+64) U(k:k+64, ki:ki+64) of the outer panel's first step (a
-// 4 x 4 register tile per thread).  Unblocked right-looking elimination in
-// shared memory: the pivot column is scaled by the reciprocal of the pivot,
-// then the trailing block takes the rank-1 update, and the same row
-// operations on an identity block give L11^-1.  A backward sweep over the
-// rows of [U | I] then gives U11^-1.  Both go to the instance's slot of S.inv as
+// L(ki:ki+64, k:k+64) U(k:k+64, ki:ki+64) of the outer panel's first step.
+// Unblocked right-looking elimination: the pivot column is scaled by the
+// reciprocal of the pivot, then the trailing block takes the rank-1 update,
+// and the same row operations on an identity block give L11^-1.  A backward
+// sweep over the rows of [U | I] then gives U11^-1.  Both go to the instance's
+// slot of S.inv as
 //   ui[q * 64 + c] = U11^-1(q, c),  li[q * 64 + r] = L11^-1(r, q)
 // (zero outside the triangles), the operands the panel kernel multiplies by.
-// Shared memory (dynamic): D[c][r] = A(ki + r, ki + c), and two work arrays
-// that hold the PRE operands first and the inverses afterwards.
+// Thread (tr, tc) = (tid / 4, tid % 4) holds, in registers, the entries of row
+// tr in the columns c = tc + 4i (i < 16) of D, of L11^-1 and of U11^-1.  Per
+// pivot p the threads of row p publish their row to a double-buffered shared
+// row (one barrier per pivot), the multiplier of row tr comes from its owner
+// by a shuffle among the row's four lanes, and every update is unrolled.
+// Shared memory (dynamic, PRE only): W1[q][r] = L(ki + r, k + q), W2[c][q] =
+// U(k + q, ki + c).
 // ---------------------------------------------------------------------------
-constexpr size_t kImDiagSmem = 3 * 64 * kPitch * sizeof(float);
-constexpr int kInvPitch = 65;  // inverse arrays: a thread per column, rows across the warp
+constexpr size_t kImDiagSmemPre = 2 * 64 * kPitch * sizeof(float);
 
 template <bool PRE>
-__global__ void __launch_bounds__(kImDiagThreads) k_im_diag(DevPlan P, DevState S, int k, int ki,
+__global__ void __launch_bounds__(kImDiagThreads, PRE ? 2 : 3) k_im_diag(DevPlan P, DevState S, int k, int ki,
                                                             const int32_t* __restrict__ gate) {
   extern __shared__ __align__(16) float diag_smem[];
-  float(*D)[kPitch] = reinterpret_cast<float(*)[kPitch]>(diag_smem);
-  float(*W1)[kPitch] = reinterpret_cast<float(*)[kPitch]>(diag_smem + 64 * kPitch);
-  float(*W2)[kPitch] = reinterpret_cast<float(*)[kPitch]>(diag_smem + 2 * 64 * kPitch);
-  __shared__ float invd[64];
+  __shared__ float prow[2][64], pli[2][64], invd[64];
   if (gate && *gate == 0) return;
   const int b = blockIdx.x;
   if (!S.active[b]) return;
-  const int ld = P.ndp, tid = threadIdx.x;
+  const int ld = P.ndp, tid = threadIdx.x, tc = tid & 3, tr = tid >> 2;
+  const int src0 = tid & 28;  // lane of (tr, 0)
   float* __restrict__ A = im_block(P, S, b);
-  for (int e = tid; e < 64 * 64; e += kImDiagThreads) {
-    const int c = e >> 6, r = e & 63;
-    D[c][r] = A[(size_t)(ki + c) * ld + ki + r];
-    if (PRE) {
-      W1[c][r] = A[(size_t)(k + c) * ld + ki + r];   // W1[q][r] = L(ki + r, k + q)
-      W2[c][r] = A[(size_t)(ki + c) * ld + k + r];   // W2[c][q] = U(k + q, ki + c)
-    }
-  }
-  __syncthreads();
+  float d[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) d[i] = A[(size_t)(ki + tc + 4 * i) * ld + ki + tr];
   if (PRE) {
-    const int r4 = (tid & 15) * 4, c4 = (tid >> 4) * 4;
-    float acc[4][4];
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc)
-#pragma unroll
-      for (int rr = 0; rr < 4; ++rr) acc[cc][rr] = D[c4 + cc][r4 + rr];
-#pragma unroll 2
+    float(*W1)[kPitch] = reinterpret_cast<float(*)[kPitch]>(diag_smem);
+    float(*W2)[kPitch] = reinterpret_cast<float(*)[kPitch]>(diag_smem + 64 * kPitch);
+    for (int e = tid; e < 64 * 64; e += kImDiagThreads) {
+      const int c = e >> 6, r = e & 63;
+      W1[c][r] = A[(size_t)(k + c) * ld + ki + r];
+      W2[c][r] = A[(size_t)(ki + c) * ld + k + r];
+    }
+    __syncthreads();
+    // D(tr, c) minus the products in ascending q
+#pragma unroll 1
     for (int q = 0; q < 64; q += 4) {
-      float4 u[4];
+      const float l0 = W1[q][tr], l1 = W1[q + 1][tr], l2 = W1[q + 2][tr], l3 = W1[q + 3][tr];
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) u[cc] = *reinterpret_cast<const float4*>(&W2[c4 + cc][q]);
-#pragma unroll
-      for (int qq = 0; qq < 4; ++qq) {
-        const float4 l = *reinterpret_cast<const float4*>(&W1[q + qq][r4]);
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const float uq = comp(u[cc], qq);
-          acc[cc][0] = fmaf(-l.x, uq, acc[cc][0]);
-          acc[cc][1] = fmaf(-l.y, uq, acc[cc][1]);
-          acc[cc][2] = fmaf(-l.z, uq, acc[cc][2]);
-          acc[cc][3] = fmaf(-l.w, uq, acc[cc][3]);
-        }
+      for (int i = 0; i < 16; ++i) {
+        const float4 u = *reinterpret_cast<const float4*>(&W2[tc + 4 * i][q]);
+        d[i] = fmaf(-l0, u.x, d[i]);
+        d[i] = fmaf(-l1, u.y, d[i]);
+        d[i] = fmaf(-l2, u.z, d[i]);
+        d[i] = fmaf(-l3, u.w, d[i]);
       }
     }
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc)
-#pragma unroll
-      for (int rr = 0; rr < 4; ++rr) D[c4 + cc][r4 + rr] = acc[cc][rr];
-    __syncthreads();
   }
-  // LU of D; the same row operations applied to an identity block give
-  // L11^-1 (forward elimination on [D | I]): at step p, row r > p of LI takes
-  // -L(r, p) times row p, whose entries c <= p are final.
-  //   LI[q * kInvPitch + r] = L11^-1(r, q)   (stored by column q)
-  float* UI = &W1[0][0];  // UI[q * kInvPitch + c] = U11^-1(q, c)
-  float* LI = &W2[0][0];
-  for (int e = tid; e < 64 * kInvPitch; e += kImDiagThreads) {
-    const int q = e / kInvPitch, r = e - q * kInvPitch;
-    UI[e] = (q == r) ? 1.f : 0.f;
-    LI[e] = (q == r) ? 1.f : 0.f;
-  }
-  __syncthreads();
-  // thread (tr, tc) = (tid % 64, tid / 64): row tr, every fourth column
-  const int tr = tid & 63, tc = tid >> 6;
+  float li[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) li[i] = (tc + 4 * i == tr) ? 1.f : 0.f;
+#pragma unroll
   for (int p = 0; p < 64; ++p) {
-    const float inv = 1.f / D[p][p];
-    if (tid > p && tid < 64) D[p][tid] *= inv;
+    const int buf = p & 1;
+    if (tr == p) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        prow[buf][tc + 4 * i] = d[i];
+        pli[buf][tc + 4 * i] = li[i];
+      }
+    }
     __syncthreads();
+    const float lraw = __shfl_sync(0xffffffffu, d[p >> 2], src0 | (p & 3));  // D(tr, p)
     if (tr > p) {
-      const float l = D[p][tr];
-      for (int c = p + 1 + tc; c < 64; c += 4) D[c][tr] = fmaf(-l, D[c][p], D[c][tr]);
-      // row tr of L^-1, columns q <= p
-      for (int q = tc; q <= p; q += 4) LI[q * kInvPitch + tr] = fmaf(-l, LI[q * kInvPitch + p], LI[q * kInvPitch + tr]);
+      const float inv = 1.f / prow[buf][p];
+      const float l = lraw * inv;
+      if (tc == (p & 3)) d[p >> 2] = l;
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (tc + 4 * i > p) d[i] = fmaf(-l, prow[buf][tc + 4 * i], d[i]);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (tc + 4 * i <= p) li[i] = fmaf(-l, pli[buf][tc + 4 * i], li[i]);
     }
-    __syncthreads();
-  }
-  if (tid < 64) invd[tid] = 1.f / D[tid][tid];
-  __syncthreads();
-  // U11^-1 by a backward sweep over the rows of [U | I]: at step p, row p is
-  // final once scaled by 1/U(p,p); rows r < p take -U(r, p) times it.  Each
-  // thread scales its own copy of the row-p entry, so the row is scaled in
-  // place after the barrier.
-  for (int p = 63; p >= 0; --p) {
-    if (tr < p) {
-      const float u = D[p][tr] * invd[p];
-      for (int c = p + tc; c < 64; c += 4) UI[tr * kInvPitch + c] = fmaf(-u, UI[p * kInvPitch + c], UI[tr * kInvPitch + c]);
-    }
-    __syncthreads();
-    if (tid >= p && tid < 64) UI[p * kInvPitch + tid] *= invd[p];
-    __syncthreads();
   }
   float* __restrict__ inv_out = reinterpret_cast<float*>(S.inv) + (size_t)b * 8192;
-  for (int e = tid; e < 64 * 64; e += kImDiagThreads) {
-    const int c = e >> 6, r = e & 63;
-    A[(size_t)(ki + c) * ld + ki + r] = D[c][r];
-    inv_out[e] = UI[c * kInvPitch + r];         // ui[q][c], q = e / 64
-    inv_out[4096 + e] = LI[c * kInvPitch + r];  // li[q][r]
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    A[(size_t)(ki + tc + 4 * i) * ld + ki + tr] = d[i];
+    inv_out[4096 + (tc + 4 * i) * 64 + tr] = li[i];  // li[q][r] = L11^-1(r, q)
+    if (tc + 4 * i == tr) invd[tr] = 1.f / d[i];
   }
+  float ui[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) ui[i] = (tc + 4 * i == tr) ? 1.f : 0.f;
+  __syncthreads();
+  // row p of [U | I], still unscaled, goes to the rows above it; then row p
+  // is scaled by 1 / U(p, p)
+#pragma unroll
+  for (int p = 63; p >= 0; --p) {
+    const int buf = p & 1;
+    if (tr == p) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) prow[buf][tc + 4 * i] = ui[i];
+    }
+    __syncthreads();
+    const float uraw = __shfl_sync(0xffffffffu, d[p >> 2], src0 | (p & 3));  // U(tr, p)
+    if (tr < p) {
+      const float u = uraw * invd[p];
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (tc + 4 * i >= p) ui[i] = fmaf(-u, prow[buf][tc + 4 * i], ui[i]);
+    } else if (tr == p) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (tc + 4 * i >= p) ui[i] *= invd[p];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) inv_out[tr * 64 + tc + 4 * i] = ui[i];  // ui[q][c] = U11^-1(q, c)
 }
 
 // ---------------------------------------------------------------------------
@@ -801,8 +803,7 @@ void launch_dense_im_factor(const DevPlan& P, const DevState& S, const DenseImMa
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !configured[dev]) {
     cudaFuncSetAttribute(k_im_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kImGemmSmem);
-    cudaFuncSetAttribute(k_im_diag<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kImDiagSmem);
-    cudaFuncSetAttribute(k_im_diag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kImDiagSmem);
+    cudaFuncSetAttribute(k_im_diag<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kImDiagSmemPre);
     cudaFuncSetAttribute(k_im_panel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kImPanelSmem);
     cudaFuncSetAttribute(k_im_panel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kImPanelSmemPre);
     if (dev >= 0 && dev < 64) configured[dev] = true;
@@ -812,7 +813,7 @@ void launch_dense_im_factor(const DevPlan& P, const DevState& S, const DenseImMa
   // the two 64-wide steps of the outer panel at k
   auto outer = [&](int k) {
     NRPF_LAUNCH(rec, K_DENSE_DIAG, st,
-                k_im_diag<false><<<Bp, kImDiagThreads, kImDiagSmem, st>>>(P, S, k, k, gate));
+                k_im_diag<false><<<Bp, kImDiagThreads, 0, st>>>(P, S, k, k, gate));
     int nr = ld - k - 64;
     if (nr > 0) {
       const int nch = (nr + 127) / 128;
@@ -821,7 +822,7 @@ void launch_dense_im_factor(const DevPlan& P, const DevState& S, const DenseImMa
     }
     if (ld - k < kImOuter) return;  // a last outer panel of 64
     NRPF_LAUNCH(rec, K_DENSE_DIAG, st,
-                k_im_diag<true><<<Bp, kImDiagThreads, kImDiagSmem, st>>>(P, S, k, k + 64, gate));
+                k_im_diag<true><<<Bp, kImDiagThreads, kImDiagSmemPre, st>>>(P, S, k, k + 64, gate));
     nr = ld - k - kImOuter;
     if (nr > 0) {
       const int nch = (nr + 127) / 128;
