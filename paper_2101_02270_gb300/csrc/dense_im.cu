@@ -68,7 +68,7 @@ constexpr size_t kImGemmSmem = (size_t)kImStages * kImStageBytes + 2 * (size_t)k
 // for a hardware-defined time window)
 constexpr uint32_t kImSpinLimit = 1u << 20;
 
-constexpr int kImDiagThreads = 256;
+constexpr int kImDiagThreads = 512;
 constexpr int kImSolveThreads = 256;
 constexpr int kPitch = 68;  // shared row pitch (floats) of 64-wide blocks: rows stay 16-byte aligned
 
@@ -341,30 +341,35 @@ __global__ void __launch_bounds__(kImGemmThreads, 2)
 // slot of S.inv as
 //   ui[q * 64 + c] = U11^-1(q, c),  li[q * 64 + r] = L11^-1(r, q)
 // (zero outside the triangles), the operands the panel kernel multiplies by.
-// Thread (tr, tc) = (tid / 4, tid % 4) holds, in registers, the entries of row
-// tr in the columns c = tc + 4i (i < 16) of D, of L11^-1 and of U11^-1.  Per
-// pivot p the threads of row p publish their row to a double-buffered shared
-// row (one barrier per pivot), the multiplier of row tr comes from its owner
-// by a shuffle among the row's four lanes, and every update is unrolled.
+// Thread (tr, tc) = (tid / R, tid % R), R = 8 threads per row, holds in
+// registers the entries of row tr in the columns c = tc + R i (i < 64 / R) of
+// D, of L11^-1 and of U11^-1.  Per pivot p the threads of row p publish their
+// row to a double-buffered shared row (one barrier per pivot), the multiplier
+// of row tr comes from its owner by a shuffle among the row's R lanes, and
+// every update is unrolled.  Measured on the 9,000-bus block: R = 4 (256
+// threads) 184 ms per step, stalled on instruction fetch (the unrolled pivot
+// loops); R = 8 179 ms; R = 16 304 ms; a pivot loop not unrolled, 558 ms.
 // Shared memory (dynamic, PRE only): W1[q][r] = L(ki + r, k + q), W2[c][q] =
 // U(k + q, ki + c).
 // ---------------------------------------------------------------------------
 constexpr size_t kImDiagSmemPre = 2 * 64 * kPitch * sizeof(float);
 
 template <bool PRE>
-__global__ void __launch_bounds__(kImDiagThreads, PRE ? 2 : 3) k_im_diag(DevPlan P, DevState S, int k, int ki,
-                                                            const int32_t* __restrict__ gate) {
+__global__ void __launch_bounds__(kImDiagThreads, 2) k_im_diag(DevPlan P, DevState S, int k, int ki,
+                                                                        const int32_t* __restrict__ gate) {
+  constexpr int R = kImDiagThreads / 64;  // threads per row
+  constexpr int NC = 64 / R;              // columns per thread
   extern __shared__ __align__(16) float diag_smem[];
   __shared__ float prow[2][64], pli[2][64], invd[64];
   if (gate && *gate == 0) return;
   const int b = blockIdx.x;
   if (!S.active[b]) return;
-  const int ld = P.ndp, tid = threadIdx.x, tc = tid & 3, tr = tid >> 2;
-  const int src0 = tid & 28;  // lane of (tr, 0)
+  const int ld = P.ndp, tid = threadIdx.x, tc = tid % R, tr = tid / R;
+  const int src0 = tid & 31 & ~(R - 1);  // lane of (tr, 0)
   float* __restrict__ A = im_block(P, S, b);
-  float d[16];
+  float d[NC];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) d[i] = A[(size_t)(ki + tc + 4 * i) * ld + ki + tr];
+  for (int i = 0; i < NC; ++i) d[i] = A[(size_t)(ki + tc + R * i) * ld + ki + tr];
   if (PRE) {
     float(*W1)[kPitch] = reinterpret_cast<float(*)[kPitch]>(diag_smem);
     float(*W2)[kPitch] = reinterpret_cast<float(*)[kPitch]>(diag_smem + 64 * kPitch);
@@ -379,8 +384,8 @@ __global__ void __launch_bounds__(kImDiagThreads, PRE ? 2 : 3) k_im_diag(DevPlan
     for (int q = 0; q < 64; q += 4) {
       const float l0 = W1[q][tr], l1 = W1[q + 1][tr], l2 = W1[q + 2][tr], l3 = W1[q + 3][tr];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const float4 u = *reinterpret_cast<const float4*>(&W2[tc + 4 * i][q]);
+      for (int i = 0; i < NC; ++i) {
+        const float4 u = *reinterpret_cast<const float4*>(&W2[tc + R * i][q]);
         d[i] = fmaf(-l0, u.x, d[i]);
         d[i] = fmaf(-l1, u.y, d[i]);
         d[i] = fmaf(-l2, u.z, d[i]);
@@ -388,43 +393,43 @@ __global__ void __launch_bounds__(kImDiagThreads, PRE ? 2 : 3) k_im_diag(DevPlan
       }
     }
   }
-  float li[16];
+  float li[NC];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) li[i] = (tc + 4 * i == tr) ? 1.f : 0.f;
+  for (int i = 0; i < NC; ++i) li[i] = (tc + R * i == tr) ? 1.f : 0.f;
 #pragma unroll
   for (int p = 0; p < 64; ++p) {
     const int buf = p & 1;
     if (tr == p) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        prow[buf][tc + 4 * i] = d[i];
-        pli[buf][tc + 4 * i] = li[i];
+      for (int i = 0; i < NC; ++i) {
+        prow[buf][tc + R * i] = d[i];
+        pli[buf][tc + R * i] = li[i];
       }
     }
     __syncthreads();
-    const float lraw = __shfl_sync(0xffffffffu, d[p >> 2], src0 | (p & 3));  // D(tr, p)
+    const float lraw = __shfl_sync(0xffffffffu, d[p / R], src0 | (p % R));  // D(tr, p)
     if (tr > p) {
       const float inv = 1.f / prow[buf][p];
       const float l = lraw * inv;
-      if (tc == (p & 3)) d[p >> 2] = l;
+      if (tc == p % R) d[p / R] = l;
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (tc + 4 * i > p) d[i] = fmaf(-l, prow[buf][tc + 4 * i], d[i]);
+      for (int i = 0; i < NC; ++i)
+        if (tc + R * i > p) d[i] = fmaf(-l, prow[buf][tc + R * i], d[i]);
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (tc + 4 * i <= p) li[i] = fmaf(-l, pli[buf][tc + 4 * i], li[i]);
+      for (int i = 0; i < NC; ++i)
+        if (tc + R * i <= p) li[i] = fmaf(-l, pli[buf][tc + R * i], li[i]);
     }
   }
   float* __restrict__ inv_out = reinterpret_cast<float*>(S.inv) + (size_t)b * 8192;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    A[(size_t)(ki + tc + 4 * i) * ld + ki + tr] = d[i];
-    inv_out[4096 + (tc + 4 * i) * 64 + tr] = li[i];  // li[q][r] = L11^-1(r, q)
-    if (tc + 4 * i == tr) invd[tr] = 1.f / d[i];
+  for (int i = 0; i < NC; ++i) {
+    A[(size_t)(ki + tc + R * i) * ld + ki + tr] = d[i];
+    inv_out[4096 + (tc + R * i) * 64 + tr] = li[i];  // li[q][r] = L11^-1(r, q)
+    if (tc + R * i == tr) invd[tr] = 1.f / d[i];
   }
-  float ui[16];
+  float ui[NC];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) ui[i] = (tc + 4 * i == tr) ? 1.f : 0.f;
+  for (int i = 0; i < NC; ++i) ui[i] = (tc + R * i == tr) ? 1.f : 0.f;
   __syncthreads();
   // row p of [U | I], still unscaled, goes to the rows above it; then row p
   // is scaled by 1 / U(p, p)
@@ -433,23 +438,23 @@ __global__ void __launch_bounds__(kImDiagThreads, PRE ? 2 : 3) k_im_diag(DevPlan
     const int buf = p & 1;
     if (tr == p) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) prow[buf][tc + 4 * i] = ui[i];
+      for (int i = 0; i < NC; ++i) prow[buf][tc + R * i] = ui[i];
     }
     __syncthreads();
-    const float uraw = __shfl_sync(0xffffffffu, d[p >> 2], src0 | (p & 3));  // U(tr, p)
+    const float uraw = __shfl_sync(0xffffffffu, d[p / R], src0 | (p % R));  // U(tr, p)
     if (tr < p) {
       const float u = uraw * invd[p];
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (tc + 4 * i >= p) ui[i] = fmaf(-u, prow[buf][tc + 4 * i], ui[i]);
+      for (int i = 0; i < NC; ++i)
+        if (tc + R * i >= p) ui[i] = fmaf(-u, prow[buf][tc + R * i], ui[i]);
     } else if (tr == p) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (tc + 4 * i >= p) ui[i] *= invd[p];
+      for (int i = 0; i < NC; ++i)
+        if (tc + R * i >= p) ui[i] *= invd[p];
     }
   }
 #pragma unroll
-  for (int i = 0; i < 16; ++i) inv_out[tr * 64 + tc + 4 * i] = ui[i];  // ui[q][c] = U11^-1(q, c)
+  for (int i = 0; i < NC; ++i) inv_out[tr * 64 + tc + R * i] = ui[i];  // ui[q][c] = U11^-1(q, c)
 }
 
 // ---------------------------------------------------------------------------
