@@ -475,9 +475,21 @@ __global__ void __launch_bounds__(kImDiagThreads, 2) k_im_diag(DevPlan P, DevSta
 // 1).
 // ---------------------------------------------------------------------------
 constexpr int kImPanelThreads2 = 128;
-// Pk (reused for T2 once the left-looking product is done), Qk, Q2
-constexpr size_t kImPanelSmemPre = (size_t)(64 * 128 + 64 * 64 + 64 * 64) * sizeof(float);
-constexpr size_t kImPanelSmem = (size_t)(64 * 128 + 64 * 64) * sizeof(float);
+// row pitch of T2 (floats): with 132 a quarter warp's 16-byte stores of four
+// rows n = no + 16g + r meet 2-way bank conflicts instead of 4-way
+constexpr int kT2Pitch = 132;
+// Pk (reused for T2 once the left-looking product is done), Q2, Qk
+constexpr size_t kImPanelSmemPre = (size_t)(64 * kT2Pitch + 64 * 64 + 64 * 64) * sizeof(float);
+constexpr size_t kImPanelSmem = (size_t)(64 * kT2Pitch + 64 * 64) * sizeof(float);
+
+// 16-byte asynchronous copy global -> shared (no register staging)
+__device__ __forceinline__ void cp16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp16_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
 
 // acc[h][g][r][p] holds rows (2p, 2p+1) of the thread's 4-row group h,
 // column (g, r); one packed two-wide FMA per pair (same rounding as fmaf)
@@ -507,8 +519,8 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
                                                                const int32_t* __restrict__ gate) {
   extern __shared__ __align__(16) float pan_smem[];
   float* Pk = pan_smem;                           // PRE: [64 q][128 m]
-  float* T2 = pan_smem;                           // [64 n][128 m]: the first result, k-major (over Pk)
-  float* Q2 = pan_smem + 64 * 128;                // [64 q][64 n]: the inverse factor
+  float* T2 = pan_smem;                           // [64 n][kT2Pitch]: the first result, k-major (over Pk)
+  float* Q2 = pan_smem + 64 * kT2Pitch;           // [64 q][64 n]: the inverse factor
   float* Qk = Q2 + 64 * 64;                       // PRE: [64 q][64 n]
   if (gate && *gate == 0) return;
   const int per = 2 * nch;
@@ -523,22 +535,27 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
   const int base = ki + 64 + (rows ? task : task - nch) * 128;  // first row (rows) or column (columns)
   const int mvalid = min(128, ld - base);
   const bool active = wm * 64 < mvalid;
+  // operands: contiguous 16-byte words by asynchronous copies, all in flight
+  // together; the transposed ones through registers, fully unrolled
   {
-    const float4* src = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(S.inv) + (size_t)b * 8192 +
-                                                        (rows ? 0 : 4096));
-    for (int e = tid; e < 64 * 16; e += kImPanelThreads2) reinterpret_cast<float4*>(Q2)[e] = src[e];
+    const float* src = reinterpret_cast<const float*>(S.inv) + (size_t)b * 8192 + (rows ? 0 : 4096);
+#pragma unroll
+    for (int j = 0; j < 64 * 16 / kImPanelThreads2; ++j) {
+      const int e = tid + j * kImPanelThreads2;
+      cp16(Q2 + 4 * e, src + 4 * e);
+    }
   }
   if (PRE) {
     if (rows) {
       // Pk[q][m] = L(base + m, k + q); Qk[q][n] = U(k + q, ki + n)
-      for (int e = tid; e < 64 * 32; e += kImPanelThreads2) {
-        const int q = e >> 5, m4 = e & 31;
-        if (4 * m4 < mvalid)
-          reinterpret_cast<float4*>(Pk + q * 128)[m4] =
-              *reinterpret_cast<const float4*>(A + (size_t)(k + q) * ld + base + 4 * m4);
+#pragma unroll
+      for (int j = 0; j < 64 * 32 / kImPanelThreads2; ++j) {
+        const int e = tid + j * kImPanelThreads2, q = e >> 5, m4 = e & 31;
+        if (4 * m4 < mvalid) cp16(Pk + q * 128 + 4 * m4, A + (size_t)(k + q) * ld + base + 4 * m4);
       }
-      for (int e = tid; e < 64 * 16; e += kImPanelThreads2) {
-        const int n = e & 63, q4 = e >> 6;
+#pragma unroll
+      for (int j = 0; j < 64 * 16 / kImPanelThreads2; ++j) {
+        const int e = tid + j * kImPanelThreads2, n = e & 63, q4 = e >> 6;
         const float4 v = *reinterpret_cast<const float4*>(A + (size_t)(ki + n) * ld + k + 4 * q4);
         Qk[(4 * q4) * 64 + n] = v.x;
         Qk[(4 * q4 + 1) * 64 + n] = v.y;
@@ -547,8 +564,14 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
       }
     } else {
       // Pk[q][m] = U(k + q, base + m); Qk[q][n] = L(ki + n, k + q)
-      for (int e = tid; e < 128 * 16; e += kImPanelThreads2) {
-        const int m = e & 127, q4 = e >> 7;
+#pragma unroll
+      for (int j = 0; j < 64 * 16 / kImPanelThreads2; ++j) {
+        const int e = tid + j * kImPanelThreads2, q = e >> 4, n4 = e & 15;
+        cp16(Qk + q * 64 + 4 * n4, A + (size_t)(k + q) * ld + ki + 4 * n4);
+      }
+#pragma unroll
+      for (int j = 0; j < 128 * 16 / kImPanelThreads2; ++j) {
+        const int e = tid + j * kImPanelThreads2, m = e & 127, q4 = e >> 7;
         if (m < mvalid) {
           const float4 v = *reinterpret_cast<const float4*>(A + (size_t)(base + m) * ld + k + 4 * q4);
           Pk[(4 * q4) * 128 + m] = v.x;
@@ -556,11 +579,6 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
           Pk[(4 * q4 + 2) * 128 + m] = v.z;
           Pk[(4 * q4 + 3) * 128 + m] = v.w;
         }
-      }
-      for (int e = tid; e < 64 * 16; e += kImPanelThreads2) {
-        const int q = e >> 4, n4 = e & 15;
-        reinterpret_cast<float4*>(Qk + q * 64)[n4] =
-            *reinterpret_cast<const float4*>(A + (size_t)(k + q) * ld + ki + 4 * n4);
       }
     }
   }
@@ -595,6 +613,7 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
           }
     }
   }
+  cp16_wait_all();
   __syncthreads();
   if (PRE && active) {
 #pragma unroll 4
@@ -614,7 +633,7 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
       for (int g = 0; g < 2; ++g)
 #pragma unroll
         for (int r = 0; r < 4; ++r)
-          *reinterpret_cast<float4*>(T2 + (no + 16 * g + r) * 128 + mo + 32 * h) =
+          *reinterpret_cast<float4*>(T2 + (no + 16 * g + r) * kT2Pitch + mo + 32 * h) =
               make_float4(acc[h][g][r][0].x, acc[h][g][r][0].y, acc[h][g][r][1].x, acc[h][g][r][1].y);
   }
   __syncthreads();
@@ -631,8 +650,8 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
   const int qend = 32 * (wn + 1);
 #pragma unroll 4
   for (int q = 0; q < qend; ++q) {
-    const float4 a[2] = {*reinterpret_cast<const float4*>(T2 + q * 128 + mo),
-                         *reinterpret_cast<const float4*>(T2 + q * 128 + mo + 32)};
+    const float4 a[2] = {*reinterpret_cast<const float4*>(T2 + q * kT2Pitch + mo),
+                         *reinterpret_cast<const float4*>(T2 + q * kT2Pitch + mo + 32)};
     const float4 bq[2] = {*reinterpret_cast<const float4*>(Q2 + q * 64 + no),
                           *reinterpret_cast<const float4*>(Q2 + q * 64 + no + 16)};
     fma_q(acc, a, bq, 1.f);
