@@ -81,6 +81,15 @@ __device__ __forceinline__ uint32_t su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// 16-byte asynchronous copy global -> shared (no register staging)
+__device__ __forceinline__ void cp16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp16_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void bar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
 }
@@ -373,11 +382,13 @@ __global__ void __launch_bounds__(kImDiagThreads, 2) k_im_diag(DevPlan P, DevSta
   if (PRE) {
     float(*W1)[kPitch] = reinterpret_cast<float(*)[kPitch]>(diag_smem);
     float(*W2)[kPitch] = reinterpret_cast<float(*)[kPitch]>(diag_smem + 64 * kPitch);
-    for (int e = tid; e < 64 * 64; e += kImDiagThreads) {
-      const int c = e >> 6, r = e & 63;
-      W1[c][r] = A[(size_t)(k + c) * ld + ki + r];
-      W2[c][r] = A[(size_t)(ki + c) * ld + k + r];
+#pragma unroll
+    for (int j = 0; j < 64 * 16 / kImDiagThreads; ++j) {
+      const int e = tid + j * kImDiagThreads, c = e >> 4, r4 = 4 * (e & 15);
+      cp16(&W1[c][r4], A + (size_t)(k + c) * ld + ki + r4);
+      cp16(&W2[c][r4], A + (size_t)(ki + c) * ld + k + r4);
     }
+    cp16_wait_all();
     __syncthreads();
     // D(tr, c) minus the products in ascending q
 #pragma unroll 1
@@ -482,14 +493,6 @@ constexpr int kT2Pitch = 132;
 constexpr size_t kImPanelSmemPre = (size_t)(64 * kT2Pitch + 64 * 64 + 64 * 64) * sizeof(float);
 constexpr size_t kImPanelSmem = (size_t)(64 * kT2Pitch + 64 * 64) * sizeof(float);
 
-// 16-byte asynchronous copy global -> shared (no register staging)
-__device__ __forceinline__ void cp16(float* dst, const float* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp16_wait_all() {
-  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-}
 
 // acc[h][g][r][p] holds rows (2p, 2p+1) of the thread's 4-row group h,
 // column (g, r); one packed two-wide FMA per pair (same rounding as fmaf)
