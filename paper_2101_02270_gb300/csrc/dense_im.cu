@@ -486,11 +486,14 @@ __global__ void __launch_bounds__(kImDiagThreads, 2) k_im_diag(DevPlan P, DevSta
 // 1).
 // ---------------------------------------------------------------------------
 constexpr int kImPanelThreads2 = 128;
-// row pitch of T2 (floats): with 132 a quarter warp's 16-byte stores of four
-// rows n = no + 16g + r meet 2-way bank conflicts instead of 4-way
+// row pitches (floats) of Pk / T2 and of Qk: with 132 and 68 the stores that
+// transpose (a quarter warp's 16-byte stores of four rows n = no + 16g + r of
+// T2; scalar stores of four rows 4 q4 + c of Pk or Qk) meet 2-way bank
+// conflicts instead of 4-way
 constexpr int kT2Pitch = 132;
+constexpr int kQkPitch = 68;
 // Pk (reused for T2 once the left-looking product is done), Q2, Qk
-constexpr size_t kImPanelSmemPre = (size_t)(64 * kT2Pitch + 64 * 64 + 64 * 64) * sizeof(float);
+constexpr size_t kImPanelSmemPre = (size_t)(64 * kT2Pitch + 64 * 64 + 64 * kQkPitch) * sizeof(float);
 constexpr size_t kImPanelSmem = (size_t)(64 * kT2Pitch + 64 * 64) * sizeof(float);
 
 
@@ -521,10 +524,10 @@ template <bool PRE>
 __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, DevState S, int k, int ki, int nch,
                                                                const int32_t* __restrict__ gate) {
   extern __shared__ __align__(16) float pan_smem[];
-  float* Pk = pan_smem;                           // PRE: [64 q][128 m]
+  float* Pk = pan_smem;                           // PRE: [64 q][kT2Pitch]
   float* T2 = pan_smem;                           // [64 n][kT2Pitch]: the first result, k-major (over Pk)
   float* Q2 = pan_smem + 64 * kT2Pitch;           // [64 q][64 n]: the inverse factor
-  float* Qk = Q2 + 64 * 64;                       // PRE: [64 q][64 n]
+  float* Qk = Q2 + 64 * 64;                       // PRE: [64 q][kQkPitch]
   if (gate && *gate == 0) return;
   const int per = 2 * nch;
   const int b = (int)(blockIdx.x / (unsigned)per);
@@ -548,39 +551,42 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
       cp16(Q2 + 4 * e, src + 4 * e);
     }
   }
+  // The transposed operands are read four 16-byte words of one column per
+  // four lanes (64-byte segments): lanes (c4 = lane % 4, the column from the
+  // rest), word q4 = c4 + 4 (j % 4).
   if (PRE) {
     if (rows) {
       // Pk[q][m] = L(base + m, k + q); Qk[q][n] = U(k + q, ki + n)
 #pragma unroll
       for (int j = 0; j < 64 * 32 / kImPanelThreads2; ++j) {
         const int e = tid + j * kImPanelThreads2, q = e >> 5, m4 = e & 31;
-        if (4 * m4 < mvalid) cp16(Pk + q * 128 + 4 * m4, A + (size_t)(k + q) * ld + base + 4 * m4);
+        if (4 * m4 < mvalid) cp16(Pk + q * kT2Pitch + 4 * m4, A + (size_t)(k + q) * ld + base + 4 * m4);
       }
 #pragma unroll
       for (int j = 0; j < 64 * 16 / kImPanelThreads2; ++j) {
-        const int e = tid + j * kImPanelThreads2, n = e & 63, q4 = e >> 6;
+        const int n = (tid >> 2) + 32 * (j >> 2), q4 = (tid & 3) + 4 * (j & 3);
         const float4 v = *reinterpret_cast<const float4*>(A + (size_t)(ki + n) * ld + k + 4 * q4);
-        Qk[(4 * q4) * 64 + n] = v.x;
-        Qk[(4 * q4 + 1) * 64 + n] = v.y;
-        Qk[(4 * q4 + 2) * 64 + n] = v.z;
-        Qk[(4 * q4 + 3) * 64 + n] = v.w;
+        Qk[(4 * q4) * kQkPitch + n] = v.x;
+        Qk[(4 * q4 + 1) * kQkPitch + n] = v.y;
+        Qk[(4 * q4 + 2) * kQkPitch + n] = v.z;
+        Qk[(4 * q4 + 3) * kQkPitch + n] = v.w;
       }
     } else {
       // Pk[q][m] = U(k + q, base + m); Qk[q][n] = L(ki + n, k + q)
 #pragma unroll
       for (int j = 0; j < 64 * 16 / kImPanelThreads2; ++j) {
         const int e = tid + j * kImPanelThreads2, q = e >> 4, n4 = e & 15;
-        cp16(Qk + q * 64 + 4 * n4, A + (size_t)(k + q) * ld + ki + 4 * n4);
+        cp16(Qk + q * kQkPitch + 4 * n4, A + (size_t)(k + q) * ld + ki + 4 * n4);
       }
 #pragma unroll
       for (int j = 0; j < 128 * 16 / kImPanelThreads2; ++j) {
-        const int e = tid + j * kImPanelThreads2, m = e & 127, q4 = e >> 7;
+        const int m = (tid >> 2) + 32 * (j >> 2), q4 = (tid & 3) + 4 * (j & 3);
         if (m < mvalid) {
           const float4 v = *reinterpret_cast<const float4*>(A + (size_t)(base + m) * ld + k + 4 * q4);
-          Pk[(4 * q4) * 128 + m] = v.x;
-          Pk[(4 * q4 + 1) * 128 + m] = v.y;
-          Pk[(4 * q4 + 2) * 128 + m] = v.z;
-          Pk[(4 * q4 + 3) * 128 + m] = v.w;
+          Pk[(4 * q4) * kT2Pitch + m] = v.x;
+          Pk[(4 * q4 + 1) * kT2Pitch + m] = v.y;
+          Pk[(4 * q4 + 2) * kT2Pitch + m] = v.z;
+          Pk[(4 * q4 + 3) * kT2Pitch + m] = v.w;
         }
       }
     }
@@ -621,10 +627,10 @@ __global__ void __launch_bounds__(kImPanelThreads2, 3) k_im_panel(DevPlan P, Dev
   if (PRE && active) {
 #pragma unroll 4
     for (int q = 0; q < 64; ++q) {
-      const float4 a[2] = {*reinterpret_cast<const float4*>(Pk + q * 128 + mo),
-                           *reinterpret_cast<const float4*>(Pk + q * 128 + mo + 32)};
-      const float4 bq[2] = {*reinterpret_cast<const float4*>(Qk + q * 64 + no),
-                            *reinterpret_cast<const float4*>(Qk + q * 64 + no + 16)};
+      const float4 a[2] = {*reinterpret_cast<const float4*>(Pk + q * kT2Pitch + mo),
+                           *reinterpret_cast<const float4*>(Pk + q * kT2Pitch + mo + 32)};
+      const float4 bq[2] = {*reinterpret_cast<const float4*>(Qk + q * kQkPitch + no),
+                            *reinterpret_cast<const float4*>(Qk + q * kQkPitch + no + 16)};
       fma_q(acc, a, bq, -1.f);
     }
   }
