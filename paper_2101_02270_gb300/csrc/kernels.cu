@@ -737,17 +737,18 @@ __global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevP
   T acc[TS][TS];
   if constexpr (DenseGroup<T>::G == 4 && TS == 8) {
     // FP32, grouped rows: rows r..r+3 of column c for this lane are the
-    // float4 at index (c * ld + r) * 8 + lane
+    // float4 at index (c * ld + r) * 8 + lane.  acc2[p][c] holds rows 2p,
+    // 2p+1 of column c: one packed two-wide FMA (fma.rn.f32x2) per pair, with
+    // -b, which rounds as acc - a b in one step
     float4* __restrict__ A4 = reinterpret_cast<float4*>(Ab);
+    float2 acc2[4][TS];
 #pragma unroll
     for (int c = 0; c < TS; ++c)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const float4 v = A4[((size_t)(j0 + c) * ld + i0 + 4 * h) * 8 + lane];
-        acc[4 * h][c] = v.x;
-        acc[4 * h + 1][c] = v.y;
-        acc[4 * h + 2][c] = v.z;
-        acc[4 * h + 3][c] = v.w;
+        acc2[2 * h][c] = make_float2(v.x, v.y);
+        acc2[2 * h + 1][c] = make_float2(v.z, v.w);
       }
 #pragma unroll(KB > 16 ? 2 : KB / 4)
     for (int pp = 0; pp < KB / 4; ++pp) {
@@ -759,12 +760,14 @@ __global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevP
         const int p = 4 * pp + q;
         const float4 a0 = A4[((size_t)(k + p) * ld + i0) * 8 + lane];  // rows i0..i0+7 of column k+p (L21)
         const float4 a1 = A4[((size_t)(k + p) * ld + i0 + 4) * 8 + lane];
-        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float2 ap[4] = {make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(a1.x, a1.y),
+                              make_float2(a1.z, a1.w)};
 #pragma unroll
         for (int c = 0; c < TS; ++c) {
-          const float b = q == 0 ? bq[c].x : q == 1 ? bq[c].y : q == 2 ? bq[c].z : bq[c].w;
+          const float nb = -(q == 0 ? bq[c].x : q == 1 ? bq[c].y : q == 2 ? bq[c].z : bq[c].w);
+          const float2 b2 = make_float2(nb, nb);
 #pragma unroll
-          for (int r = 0; r < TS; ++r) acc[r][c] -= a[r] * b;
+          for (int r = 0; r < 4; ++r) acc2[r][c] = __ffma2_rn(ap[r], b2, acc2[r][c]);
         }
       }
     }
@@ -773,7 +776,7 @@ __global__ void __launch_bounds__(128, UpdOcc<T, TS>::value) k_dense_update(DevP
 #pragma unroll
       for (int h = 0; h < 2; ++h)
         A4[((size_t)(j0 + c) * ld + i0 + 4 * h) * 8 + lane] =
-            make_float4(acc[4 * h][c], acc[4 * h + 1][c], acc[4 * h + 2][c], acc[4 * h + 3][c]);
+            make_float4(acc2[2 * h][c].x, acc2[2 * h][c].y, acc2[2 * h + 1][c].x, acc2[2 * h + 1][c].y);
   } else if constexpr (DenseGroup<T>::G == 1) {
     // element (r, c) is Ab[(c * ld + r) * 32 + lane]: a column pointer plus a
     // compile-time offset for every access
