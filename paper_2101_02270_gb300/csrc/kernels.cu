@@ -452,11 +452,11 @@ __global__ void __launch_bounds__(32 * kLWarps) k_lu_sparse_level(DevPlan P, Dev
 //   per SM, the shared-memory limit.
 //   FP32 (bound by load latency): each row starts from 0, sums the products
 //   and is subtracted from A(i, j) at the end, which keeps the register count
-//   and so the warps per SM up.
+//   and so the warps per SM up (at most 48 registers: ten CTAs per SM).
 constexpr int kSchurWarps = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(32 * kSchurWarps, sizeof(T) == 8 ? 7 : 1) k_schur(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
+__global__ void __launch_bounds__(32 * kSchurWarps, sizeof(T) == 8 ? 7 : 10) k_schur(DevPlan P, DevState S, const int32_t* __restrict__ gate) {
   if (gate && *gate == 0) return;
   __shared__ T acc[kSchurWarps][32][33];  // [row of the chunk][lane], padded: a row of one lane is read across the warp
   const int lane = threadIdx.x, w = threadIdx.y;
