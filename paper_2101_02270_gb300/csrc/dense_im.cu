@@ -125,7 +125,8 @@ __device__ __forceinline__ float comp(const float4& v, int q) {
 }
 
 // ---------------------------------------------------------------------------
-// Trailing update C -= A B of one 128 x 128 tile of one instance.
+// Update C -= A B of one 128 x 128 tile of one instance, over the depth of the
+// pivot columns k .. k + 32 nkc - 1, the tile held in registers throughout.
 // Per chunk of depth 32, TMA lands the A chunk (As[kk][i] = A(i0 + i, k + 32 kc
 // + kk), 512 bytes per kk) and the B chunk as 128 rows of 128 bytes (row j =
 // B(k + 32 kc + 0..31, j0 + j), 16-byte chunk q stored at chunk q ^ (j % 8):
