@@ -350,8 +350,10 @@ def combine_ranks(ms, converged, device):
 # GPU arm
 # ---------------------------------------------------------------------------
 # ncu DRAM bytes over algorithmic bytes of the depth-64 FP32 trailing update
-# (371.7 MB of 419.4 MB, profiles/dense_update_fp32_mesh2000.md).
-DENSE_UPDATE_FP32_DRAM_PER_ALG = 371.7 / 419.4
+# of the interleaved layout; None: the kernel changed (packed two-wide FMAs)
+# after the capture in profiles/dense_update_fp32_mesh2000.md (371.7 MB of
+# 419.4 MB), which is not repeated for it.
+DENSE_UPDATE_FP32_DRAM_PER_ALG = None
 
 # ncu DRAM bytes (read + write) of one k_im_gemm launch over its algorithmic
 # bytes (im_update_bytes), from the capture summarised in
@@ -947,7 +949,8 @@ def measure_mesh(args, pf, name, lu, steps, warmup, dev, rank=0, world=1, with_c
         gbs = du_bytes / (du[2] / 1e3) / 1e9 if du[2] > 0 else None
         roof = {"bound": "hbm", "kernel": "dense_update", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                 "frac": (gbs / hbm) if gbs else None,
-                "traffic": DENSE_UPDATE_FP32_DRAM_PER_ALG * du_bytes / max(active_launches, 1),
+                "traffic": (DENSE_UPDATE_FP32_DRAM_PER_ALG * du_bytes / max(active_launches, 1)
+                            if DENSE_UPDATE_FP32_DRAM_PER_ALG is not None else None),
                 "traffic_kind": "ncu DRAM bytes / algorithmic bytes of a batch-640 depth-64 capture, times the "
                                 "algorithmic bytes per launch",
                 "peak_kind": f"{hbm_kind} HBM copy bandwidth", "fp32_tflops": achieved, "fp32_peak_tflops": fp32_peak,
