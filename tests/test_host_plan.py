@@ -296,3 +296,22 @@ def test_instance_major_update_accounting_matches_lu_arithmetic():
                 nr1 = n - k - 128
                 other += 64 ** 3 + diag + nr1 * (2 * 64 * 64 + row_solve + col_solve)
         assert gemm + other == total, n
+
+
+def test_instance_major_update_bytes_match_a_brute_force_count():
+    """bench.py's algorithmic bytes of a block update (its block column and row
+    read and written once, L(kj:, :kj) and U(:kj, kj:) read once) equal a
+    count of the distinct entries each touches, on blocks with and without a
+    last outer panel of 64."""
+    import importlib.util
+    import pathlib
+    spec = importlib.util.spec_from_file_location("bench", pathlib.Path(__file__).parent.parent / "bench.py")
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for n in (192, 320, 384):
+        for kj in range(128, n, 128):
+            c_entries = {(r, c) for r in range(kj, n) for c in range(kj, min(kj + 128, n))}
+            c_entries |= {(r, c) for r in range(kj, min(kj + 128, n)) for c in range(kj + 128, n)}
+            l_entries = {(r, p) for r in range(kj, n) for p in range(kj)}
+            u_entries = {(p, c) for p in range(kj) for c in range(kj, n)}
+            assert bench.im_update_bytes(n, kj) == 8 * len(c_entries) + 4 * (len(l_entries) + len(u_entries)), (n, kj)
