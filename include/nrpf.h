@@ -58,7 +58,8 @@ extern "C" {
                                     instances of a tile (one lane each)        */
 #define NRPF_DENSE_INSTANCE_MAJOR 2 /* each instance's dense block its own
                                     column-major matrix, factorised by CTA-tiled
-                                    kernels (FP32 LU only, panel 64)            */
+                                    kernels, left-looking by outer panels of
+                                    128 (FP32 LU only, panel 64)                */
 #define NRPF_DENSE_IM_MIN 512
 
 typedef struct pf_options {
