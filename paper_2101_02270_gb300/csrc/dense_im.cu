@@ -49,10 +49,11 @@ constexpr int kImOuter = 128;               // outer panel width
 constexpr int kImTile = 128;                // GEMM tile (rows and columns of C)
 constexpr int kImKc = 32;                   // GEMM depth per stage
 constexpr int kImStages = 2;
-// column groups of 32 per thread in the trailing update: 2 (an 8 x 8 register
-// tile, 8 warps per CTA) or 4 (8 x 16, 4 warps).  The wider tile needs fewer
-// shared-memory wavefronts per FMA but leaves half the warps; measured on the
-// 9,000-bus trailing update it is 1 % slower, so the 8 x 8 tile is used.
+// column groups of 32 per warp in the block update (four columns of each per
+// thread): 2 (an 8 x 8 register tile, 8 warps per CTA) or 4 (8 x 16, 4 warps).
+// The wider tile needs fewer shared-memory wavefronts per FMA but leaves half
+// the warps; measured on the 9,000-bus update it is 1 % slower, so the 8 x 8
+// tile is used.
 constexpr int kImGC = 2;
 // packed two-wide FP32 FMA (fma.rn.f32x2) in the trailing update: each
 // instruction updates two rows of a column; the B chunk is negated while it is
